@@ -1,0 +1,353 @@
+#!/usr/bin/env python3
+"""Benchmark: exact sparse spherical k-means, whole clustering jobs on synthetic tf-idf data.
+
+One step = one complete clustering job (skm_fit): the Lloyd loop of the paper (Sec. 2)
+from k seeded initial documents, with the non-changing-clusters skip (Sec. 3.1), BF16
+centroids scored with FP32 accumulation, FP64 rescoring of near ties, and the
+deterministic centroid update, up to the workload's iteration limit or until no
+assignment changes. Every assignment step, update and objective runs on the GPU.
+
+Metric: documents assigned per second per iteration (N x iterations / time).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload large|medium|small]
+  python bench.py --impl reference ...   (the FP64 CPU oracle on host cores)
+
+Under torchrun (N > 1) each rank runs an independent replica (different seeds) on its
+own GPU; the job value is the sum of the ranks' documents over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "docs assigned/s per iteration"
+UNIT = "docs/s"
+FP32_LANES_PER_SM = 128
+N_SM = 152
+SM_MAX_MHZ = 2070.0
+
+
+def peaks() -> dict:
+    p = {"hbm_gbs": 6800.0, "source": "fallback"}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            m = json.load(f)
+        p = {"hbm_gbs": float(m["hbm_gbs"]), "source": "measured",
+             "sm_max_mhz": float(m.get("sm_max_mhz", SM_MAX_MHZ))}
+    # FP32 FMA peak from unit counts and the maximum SM clock: 152 SMs x 128 lanes x 2 flop
+    mhz = p.get("sm_max_mhz", SM_MAX_MHZ)
+    p["fp32_tflops"] = N_SM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    return p
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ distributed
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        import torch
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local, dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, x: float, device) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, x: float, device) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ CPU oracle legs
+def oracle_sample_rate(docs, C32: np.ndarray, seed: int, budget_s: float = 15.0):
+    """The FP64 oracle's assignment step (plain definition, Sec. 2) on a bounded, seeded
+    sample of the workload's documents: returns (docs/s, sample size, seconds, threads)."""
+    import oracle
+    from paper_2108_00895_gb300 import synth
+    probe = docs.rows(synth.sample_ids(docs.n_docs, 64, seed))
+    t0 = time.perf_counter()
+    oracle.assign(probe, C32)
+    per_doc = max((time.perf_counter() - t0) / probe.n_docs, 1e-7)
+    n = int(min(docs.n_docs, max(64, budget_s / per_doc)))
+    sample = docs.rows(synth.sample_ids(docs.n_docs, n, seed + 1))
+    t0 = time.perf_counter()
+    oracle.assign(sample, C32)
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt, oracle.num_threads()
+
+
+def run_reference(args, w, world, rank, dist):
+    """Reference arm: the FP64 oracle as it stands, timed on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2108_00895_gb300 import synth
+    docs = w.corpus()
+    ids = w.init_ids()
+    # c_j = x_{init_j}, stored as float32 (the oracle widens it exactly) to halve host memory
+    C0 = np.zeros((docs.n_terms, w.k), np.float32)
+    for j, i in enumerate(ids):
+        a, b = docs.row_ptr[i], docs.row_ptr[i + 1]
+        C0[docs.col_idx[a:b], j] = docs.values[a:b]
+    # size one step's sample so that warmup + steps stay within a few minutes
+    probe = docs.rows(synth.sample_ids(docs.n_docs, 32, 7))
+    t0 = time.perf_counter()
+    oracle.assign(probe, C0)
+    per_doc = max((time.perf_counter() - t0) / probe.n_docs, 1e-7)
+    total_budget = 150.0
+    n = int(min(docs.n_docs, max(32, total_budget / (args.steps + args.warmup) / per_doc)))
+    times = []
+    for s in range(args.warmup + args.steps):
+        sample = docs.rows(synth.sample_ids(docs.n_docs, n, 100 + s))
+        t0 = time.perf_counter()
+        oracle.assign(sample, C0)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+    ms = 1e3 * sum(times) / len(times)
+    value = n / (sum(times) / len(times))
+    cores = oracle.num_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(w.describe(), sample_docs_per_step=n, centroids="initial documents"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n} seeded documents of the workload per step, assignment "
+                                       f"step against the k initial centroids"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, w, world, rank, local, dist):
+    import torch
+
+    from paper_2108_00895_gb300 import skm
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    skm.load()
+    if rank != 0:
+        w = w.scaled(seed_id=w.seed_id + 100 * rank)
+    docs = w.corpus()
+    ids = w.init_ids()
+    N = docs.n_docs
+    d_docs = (torch.from_numpy(docs.row_ptr).to(dev), torch.from_numpy(docs.col_idx).to(dev),
+              torch.from_numpy(docs.values).to(dev))
+    stream = torch.cuda.current_stream(dev)
+    km = skm.SphericalKMeans(w.k, precision=w.precision, prune=w.prune, max_iter=w.max_iter,
+                             shift_tol=-1.0, rescore=True, tau=args.tau, device=local,
+                             stream=stream.cuda_stream, timing=True)
+    a_dev = torch.empty(N, dtype=torch.int32, device=dev)
+    for _ in range(args.warmup):
+        km.fit(d_docs, ids, n_terms=docs.n_terms, assign_out=a_dev)
+    torch.cuda.synchronize(dev)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(dist)
+    torch.cuda.synchronize(dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    iters = 0
+    agg = {"fmas": 0, "bytes": 0, "ms_score": 0.0, "ms_decide": 0.0, "ms_update": 0.0,
+           "launches_total": 0, "launches_score": 0, "sims": 0, "docs_pruned": 0, "docs_full": 0,
+           "docs_rescored": 0, "docs_rescored_full": 0}
+    objectives = None
+    for _ in range(args.steps):
+        r = km.fit(d_docs, ids, n_terms=docs.n_terms, assign_out=a_dev)
+        iters += r.iters
+        objectives = r.objective
+        for key in agg:
+            agg[key] += r.stats[key]
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(dist)
+    clk = clocks.stop()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    t_max = max_over_ranks(dist, elapsed_ms, dev)
+    docs_done = sum_over_ranks(dist, float(N * iters), dev)
+    value = docs_done / (t_max / 1e3)
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        a_host = np.empty(N, np.int32)
+        barrier(dist)
+        t0 = time.perf_counter()
+        e_iters = 0
+        for _ in range(args.steps):
+            r = km.fit(docs, ids, assign_out=a_host)
+            e_iters += r.iters
+        dt = time.perf_counter() - t0
+        dt = max_over_ranks(dist, dt, dev)
+        e_docs = sum_over_ranks(dist, float(N * e_iters), dev)
+        e2e = {"value": e_docs / dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(8 * (N + 1) + 8 * docs.nnz),
+               "d2h_bytes_per_step": int(4 * N + 8 * (e_iters // max(args.steps, 1)))}
+
+    pk = peaks()
+    fl = 2.0 * agg["fmas"]
+    score_s = agg["ms_score"] / 1e3
+    achieved_tf = fl / score_s / 1e12 if score_s > 0 else None
+    hbm_gbs = agg["bytes"] / score_s / 1e9 if score_s > 0 else None
+    t_roof = max(agg["bytes"] / (pk["hbm_gbs"] * 1e9), fl / (pk["fp32_tflops"] * 1e12))
+    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
+                "frac": achieved_tf / pk["fp32_tflops"] if achieved_tf else None,
+                "traffic": None,
+                "kernel": "k_score (scoring pass: fused CSR x term-major centroid SpMM + top-4)",
+                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)",
+                "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": pk["hbm_gbs"],
+                        "frac": hbm_gbs / pk["hbm_gbs"] if hbm_gbs else None,
+                        "peak_source": f"{pk['source']} copy bandwidth"},
+                "combined_frac": t_roof / score_s if score_s > 0 else None,
+                "algorithmic": {"flop_per_step": fl / args.steps, "bytes_per_step": agg["bytes"] / args.steps,
+                                "score_ms_per_step": agg["ms_score"] / args.steps,
+                                "decide_ms_per_step": agg["ms_decide"] / args.steps,
+                                "update_ms_per_step": agg["ms_update"] / args.steps}}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        C = km.centroids()
+        rate, n, dt, cores = oracle_sample_rate(docs, C, 4242, args.cpu_budget)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{n} seeded documents of the workload, one assignment step (plain FP64 "
+                         f"definition) against the final centroids, {dt:.1f} s"}
+    km.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if w.precision == "bf16" else "f32",
+                "data": "synthetic",
+                "config": dict(w.describe(), parallelism=f"replicas x{world}",
+                               step="one full clustering job (fit)", iterations_per_step=iters / args.steps,
+                               l2="inputs larger than L2 (CSR + centroid matrices >> 129 MB)",
+                               objective_last=float(objectives[-1]) if objectives is not None else None,
+                               tau=args.tau),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": int(agg["launches_total"]),
+                "work": {k_: v for k_, v in agg.items()}}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["large", "medium", "small"], default="large")
+    ap.add_argument("--tau", type=float, default=1e-4)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    from paper_2108_00895_gb300 import workloads
+    w = workloads.ALL[args.workload]
+    world, rank, local, dist = dist_setup(args)
+    try:
+        if args.impl == "reference":
+            run_reference(args, w, world, rank, dist)
+        else:
+            run_ours(args, w, world, rank, local, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,181 @@
+/*
+ * skm.h -- exact sparse spherical k-means on one GPU (sm_103a), C ABI.
+ *
+ * Method: Knittel, Koch, Ertl, "Efficient Sparse Spherical k-Means for Document
+ * Clustering", DocEng 2021.
+ *   - Sec. 2: documents and centroids are unit vectors; the assignment step gives each
+ *     document the centroid of largest dot product (cosine similarity); the update step
+ *     sets each centroid to the normalised sum of its members; the loop stops when no
+ *     assignment changes (or on another criterion, Sec. 4.1).
+ *   - Sec. 3.1 (non-changing clusters): a document whose cluster did not change in the
+ *     last update is compared only with the centroids that did change.
+ *
+ * Conventions shared by every entry point:
+ *   - Documents are CSR (skm_csr): row_ptr int64[N+1], col_idx int32[E] strictly
+ *     increasing within a row and in [0, n_terms), values float[E] finite and >= 0,
+ *     every row non-empty with L2 norm 1 +- 1e-5 (zero vectors are excluded, Sec. 4.1).
+ *     Violations return SKM_ERR_INVALID; nothing aborts.
+ *   - Centroids are a term-major n_terms x k matrix: entry (t, j) is term t of centroid j.
+ *   - Ties in the argmax go to the lowest centroid index.
+ *   - Arrays marked "host or device" follow skm_csr.on_device of the same call.
+ *     The caller owns every array it passes; the library only borrows it for the call.
+ *   - Calls are synchronous: when one returns, its outputs are written. Work is issued
+ *     on the stream given in skm_config (NULL = the legacy default stream).
+ *   - A context is not thread-safe; serialise calls on one context.
+ *   - On any status other than SKM_OK, skm_last_error() describes the failure and the
+ *     context stays usable (its centroids are those of the last successful update).
+ */
+#ifndef SKM_H
+#define SKM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SKM_API __attribute__((visibility("default")))
+#else
+#define SKM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct skm_ctx skm_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    SKM_OK = 0,
+    SKM_ERR_INVALID = 1, /* bad argument or malformed input */
+    SKM_ERR_OOM = 2,     /* a device allocation failed */
+    SKM_ERR_BUDGET = 3,  /* the request would exceed skm_config.mem_budget */
+    SKM_ERR_CUDA = 4,    /* a CUDA call or kernel launch failed */
+    SKM_ERR_STATE = 5,   /* call not valid in the context's state (e.g. no centroids yet) */
+    SKM_ERR_TIMEOUT = 6  /* a bounded device wait gave up */
+} skm_status;
+
+enum { SKM_FP32 = 0, SKM_BF16 = 1 };          /* centroid storage for the scoring pass */
+enum { SKM_PRUNE_NONE = 0, SKM_PRUNE_NCC = 1 }; /* Sec. 3.1 skip on or off */
+
+/* Device memory provider. alloc returns NULL on failure; free receives the same size. */
+typedef void *(*skm_alloc_fn)(size_t bytes, void *user);
+typedef void (*skm_free_fn)(void *ptr, size_t bytes, void *user);
+
+typedef struct {
+    int32_t k;            /* clusters, >= 1 */
+    int32_t precision;    /* SKM_FP32 or SKM_BF16: type of the centroid copy that is scored.
+                             An FP32 master copy is always kept for rescoring and output. */
+    int32_t prune;        /* SKM_PRUNE_NONE or SKM_PRUNE_NCC */
+    int32_t max_iter;     /* assignment steps per skm_fit, >= 1 */
+    double shift_tol;     /* stop when max_j ||c_j(new) - c_j(old)||^2 < shift_tol (Sec. 4.1);
+                             < 0 disables the test */
+    int32_t rescore;      /* 1: documents whose lower-precision top-2 margin is below the
+                             threshold are rescored in FP64 (exact argmax); 0: off */
+    double rescore_tau;   /* margin threshold; the library raises it per document to the
+                             rounding-error bound of the scoring pass */
+    size_t mem_budget;    /* bytes of device memory the context may hold; 0 = no limit */
+    int32_t device;       /* CUDA device ordinal */
+    void *stream;         /* cudaStream_t to issue work on; NULL = legacy default stream */
+    skm_alloc_fn alloc;   /* NULL: cudaMalloc / cudaFree */
+    skm_free_fn free;
+    void *alloc_user;
+    int32_t timing;       /* 1: record CUDA events around each kernel (see skm_stats) */
+} skm_config;
+
+/* Fills a config with defaults: FP32, no pruning, max_iter 20, shift test off, rescoring
+ * on with tau 0, no budget, device 0, default stream, cudaMalloc. */
+SKM_API void skm_config_default(skm_config *cfg, int32_t k);
+
+typedef struct {
+    int64_t n_docs;
+    int32_t n_terms;
+    int64_t nnz;
+    const int64_t *row_ptr; /* [n_docs + 1], row_ptr[0] = 0, row_ptr[n_docs] = nnz */
+    const int32_t *col_idx; /* [nnz] */
+    const float *values;    /* [nnz] */
+    int32_t on_device;      /* 1: the three arrays are device pointers; 0: host pointers */
+} skm_csr;
+
+/* Per-call counters (cumulative since the last skm_fit / skm_assign started). */
+typedef struct {
+    int32_t iters;              /* assignment steps run */
+    int64_t sims;               /* similarities computed (the paper's cost measure, Sec. 3) */
+    int64_t fmas;               /* algorithmic multiply-adds of the scoring passes */
+    int64_t bytes;              /* algorithmic bytes of the scoring passes (CSR + centroid
+                                   elements needed, each once, + per-document state) */
+    int64_t docs_pruned;        /* document-steps scored only against moved centroids */
+    int64_t docs_full;          /* document-steps scored against all k centroids */
+    int64_t docs_rescored;      /* document-steps rescored in FP64 from a candidate list */
+    int64_t docs_rescored_full; /* document-steps rescored in FP64 against all k */
+    int64_t moved_total;        /* sum over steps of the number of moved centroids */
+    double ms_score;            /* device time in the scoring kernels (timing = 1) */
+    double ms_decide;           /* merge, decision and FP64 rescoring kernels */
+    double ms_update;           /* centroid update kernels */
+    int64_t launches_score;     /* scoring kernel launches */
+    int64_t launches_total;     /* all kernel launches of the library */
+} skm_stats;
+
+/* Create a context on cfg->device. cfg is copied. */
+SKM_API skm_status skm_create(const skm_config *cfg, skm_ctx **out);
+
+/* Release every device allocation of the context and the context itself. NULL is a no-op. */
+SKM_API skm_status skm_destroy(skm_ctx *ctx);
+
+/* Text of the last error on this context ("" if none). Valid until the next call. */
+SKM_API const char *skm_last_error(const skm_ctx *ctx);
+
+/*
+ * Lloyd loop (Sec. 2), starting from the centroids c_j = x_{init_doc_ids[j]}.
+ * Iteration t: assignment step (with the Sec. 3.1 skip when prune = SKM_PRUNE_NCC),
+ * then the update step. Stops after max_iter assignment steps, when no assignment
+ * changed, or when the shift test passes.
+ *   docs          the collection (host or device).
+ *   init_doc_ids  host int32[k], distinct ids in [0, n_docs).
+ *   assign_out    int32[n_docs] (host or device): final assignment.
+ *   objective_out host double[max_iter], nullable: objective sum_i x_i . c_{a_i} of each
+ *                 assignment step (against the centroids it was computed with), FP64.
+ *   iters_out     host, nullable: assignment steps run.
+ * The final centroids stay resident in the context (skm_get_centroids, skm_assign).
+ */
+SKM_API skm_status skm_fit(skm_ctx *ctx, const skm_csr *docs, const int32_t *init_doc_ids,
+                   int32_t *assign_out, double *objective_out, int32_t *iters_out);
+
+/*
+ * Assignment step (Sec. 2) of new documents against the resident centroids. Every
+ * document is scored against all k centroids (there is no previous assignment to
+ * prune with), then near ties are rescored in FP64 when cfg.rescore = 1.
+ *   assign_out int32[n_docs] (host or device).
+ *   score_out  float[n_docs] (host or device), nullable: similarity of the chosen centroid
+ *              (the FP64 value where the document was rescored).
+ */
+SKM_API skm_status skm_assign(skm_ctx *ctx, const skm_csr *docs, int32_t *assign_out, float *score_out);
+
+/*
+ * Update step (Sec. 2): every cluster with members gets c_j = S_j / ||S_j||, S_j the sum
+ * of its member documents; a cluster without members keeps its centroid.
+ *   assign        int32[n_docs] (host or device), values in [0, k).
+ *   n_changed_out host, nullable: number of recomputed centroids.
+ */
+SKM_API skm_status skm_update(skm_ctx *ctx, const skm_csr *docs, const int32_t *assign,
+                      int32_t *n_changed_out);
+
+/* Replace the resident centroids with a host or device float[n_terms * k] matrix
+ * (term-major). The lower-precision copy is re-derived (round to nearest even). */
+SKM_API skm_status skm_set_centroids(skm_ctx *ctx, int32_t n_terms, const float *centroids,
+                             int32_t on_device);
+
+/* Copy the resident FP32 centroids (term-major n_terms x k) to host or device memory. */
+SKM_API skm_status skm_get_centroids(skm_ctx *ctx, float *centroids_out, int32_t on_device);
+
+/* Resident vocabulary size (0 before the first fit / set). */
+SKM_API int32_t skm_n_terms(const skm_ctx *ctx);
+
+/* Counters of the last skm_fit / skm_assign. */
+SKM_API skm_status skm_get_stats(const skm_ctx *ctx, skm_stats *out);
+
+/* Device bytes currently held by the context. */
+SKM_API size_t skm_mem_used(const skm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SKM_H */

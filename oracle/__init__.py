@@ -68,6 +68,7 @@ def _load():
                 "oracle_objective": (_D, [_I64, _P, _P, _P, _I32, _P, _INT, _P]),
                 "oracle_update": (_I32, [_I64, _P, _P, _P, _I32, _I32, _P, _P, _P, _P, _P, _P]),
                 "oracle_init_centroids": (None, [_P, _P, _P, _I32, _I32, _P, _P]),
+                "oracle_centroids_subset": (None, [_I64, _P, _P, _P, _I32, _P, _I32, _P, _P]),
                 "oracle_index_min_overlaps": (_INT, [_I32, _P, _D, _P, _P]),
                 "oracle_index_candidates": (_I64, [_I64, _P, _P, _I32, _I32, _P, _D, _P, _P, _I64]),
                 "oracle_fit": (_I32, [_I64, _P, _P, _P, _I32, _I32, _P, _I32, _D, _INT, _INT, _P,
@@ -165,6 +166,18 @@ def update(docs, a: np.ndarray, C_prev: np.ndarray, a_prev: np.ndarray | None = 
     if n < 0:
         raise MemoryError("oracle_update: allocation failed")
     return UpdateResult(C, changed, int(n), float(shift[0]), sizes)
+
+
+def centroids_subset(docs, a: np.ndarray, clusters) -> np.ndarray:
+    """Sec. 2 centroids of the listed clusters only: d x len(clusters) float64 (zero
+    column for a cluster without members)."""
+    rp, ci, va = _csr_args(docs)
+    aa = np.ascontiguousarray(a, dtype=np.int32)
+    sel = np.ascontiguousarray(clusters, dtype=np.int32)
+    out = np.empty((docs.n_terms, len(sel)), np.float64)
+    _load().oracle_centroids_subset(docs.n_docs, _ptr(rp), _ptr(ci), _ptr(va), docs.n_terms, _ptr(aa),
+                                    len(sel), _ptr(sel), _ptr(out))
+    return out
 
 
 def init_centroids(docs, k: int, init_ids: np.ndarray) -> np.ndarray:

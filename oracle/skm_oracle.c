@@ -177,6 +177,33 @@ int32_t oracle_update(int64_t n_docs, const int64_t *row_ptr, const int32_t *col
     return n_changed;
 }
 
+/*
+ * Centroids of selected clusters only (Sec. 2, same definition and summation order as
+ * oracle_update): out[t * n_sel + q] = entry t of c_{sel[q]}; a cluster without members
+ * gives a zero column. For checks on large collections where d x k would not fit.
+ */
+void oracle_centroids_subset(int64_t n_docs, const int64_t *row_ptr, const int32_t *col,
+                             const float *val, int32_t d, const int32_t *a, int32_t n_sel,
+                             const int32_t *sel, double *out) {
+    memset(out, 0, sizeof(double) * (size_t)d * (size_t)n_sel);
+    for (int32_t q = 0; q < n_sel; ++q) {
+        const int32_t j = sel[q];
+        for (int64_t i = 0; i < n_docs; ++i) {
+            if (a[i] != j) continue;
+            for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p)
+                out[(size_t)col[p] * (size_t)n_sel + (size_t)q] += (double)val[p];
+        }
+        double ss = 0.0;
+        for (int32_t t = 0; t < d; ++t) {
+            const double v = out[(size_t)t * (size_t)n_sel + (size_t)q];
+            ss += v * v;
+        }
+        if (ss == 0.0) continue;
+        const double nrm = sqrt(ss);
+        for (int32_t t = 0; t < d; ++t) out[(size_t)t * (size_t)n_sel + (size_t)q] /= nrm;
+    }
+}
+
 /* Initial centroids from k documents: c_j = x_{init_j} (R3). */
 void oracle_init_centroids(const int64_t *row_ptr, const int32_t *col, const float *val,
                            int32_t d, int32_t k, const int32_t *init_ids, double *C) {

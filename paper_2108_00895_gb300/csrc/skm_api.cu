@@ -1,0 +1,887 @@
+// C ABI of libskm (declared in include/skm.h): context, device memory, and the host side of
+// the Lloyd loop (Sec. 2 of the paper) with the non-changing-clusters skip (Sec. 3.1).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "skm.h"
+#include "skm_kernels.cuh"
+
+using namespace skm;
+
+namespace {
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct skm_ctx {
+    skm_config cfg{};
+    cudaStream_t st = nullptr;
+    std::string err;
+    size_t used = 0;
+    std::vector<Buf *> owned;
+
+    // resident centroids
+    int32_t d = 0;
+    int64_t ldc = 0;
+    int slice = 0;
+    Buf C32, C16, CM, norm_store;
+
+    // staged documents (host inputs are copied here)
+    Buf d_row_ptr, d_col, d_val;
+    // transposed postings
+    Buf col_ptr, row_idx, cval, tcount, chunk_t0, chunk_t1;
+    // per-document state
+    Buf abuf[2], s_state, r_state, clean, mdoc;
+    Buf part_s, part_j;
+    Buf list_a, list_b, rs_doc, rs_cand, refull, full64;
+    // per-cluster state
+    Buf changed, sizes, moved, pos_in_m, normsq, inv_norm, dot, shift;
+    Buf part_norm, part_dot, part_shift;
+    Buf counters, counters64, scal, obj, init_ids;
+    int32_t *h_counters = nullptr;  // pinned mirror
+    unsigned long long *h_counters64 = nullptr;
+    double *h_scal = nullptr;
+
+    skm_stats stats{};
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_score, ev_decide, ev_update;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_next = 0;
+};
+
+namespace {
+
+skm_status fail(skm_ctx *c, skm_status s, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+skm_status fail(skm_ctx *c, skm_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+    return s;
+}
+
+#define SKM_CUDA(call)                                                                     \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(ctx, SKM_ERR_CUDA, "%s failed: %s (%s:%d)", #call,                 \
+                        cudaGetErrorString(e_), __FILE__, __LINE__);                       \
+    } while (0)
+
+#define SKM_TRY(expr)                  \
+    do {                               \
+        skm_status s_ = (expr);        \
+        if (s_ != SKM_OK) return s_;   \
+    } while (0)
+
+void release(skm_ctx *ctx, Buf &b) {
+    if (!b.p) return;
+    if (ctx->cfg.free) ctx->cfg.free(b.p, b.bytes, ctx->cfg.alloc_user);
+    else cudaFree(b.p);
+    ctx->used -= b.bytes;
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+// Grow-only allocation; contents are not preserved when the buffer grows.
+skm_status ensure(skm_ctx *ctx, Buf &b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~size_t(255);
+    if (b.bytes >= bytes) return SKM_OK;
+    const size_t old = b.bytes;
+    if (ctx->cfg.mem_budget && ctx->used - old + bytes > ctx->cfg.mem_budget)
+        return fail(ctx, SKM_ERR_BUDGET, "device memory budget exceeded: %zu + %zu > %zu bytes",
+                    ctx->used - old, bytes, ctx->cfg.mem_budget);
+    release(ctx, b);
+    void *p = nullptr;
+    if (ctx->cfg.alloc) {
+        p = ctx->cfg.alloc(bytes, ctx->cfg.alloc_user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (!p) return fail(ctx, SKM_ERR_OOM, "device allocation of %zu bytes failed", bytes);
+    b.p = p;
+    b.bytes = bytes;
+    ctx->used += bytes;
+    return SKM_OK;
+}
+
+template <typename T>
+T *P(Buf &b) { return reinterpret_cast<T *>(b.p); }
+
+// ---------------------------------------------------------------- timing
+cudaEvent_t next_event(skm_ctx *ctx) {
+    if (ctx->ev_next == ctx->ev_pool.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        ctx->ev_pool.push_back(e);
+    }
+    return ctx->ev_pool[ctx->ev_next++];
+}
+
+struct Timed {
+    skm_ctx *ctx;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *v;
+    cudaEvent_t b = nullptr;
+    Timed(skm_ctx *c, std::vector<std::pair<cudaEvent_t, cudaEvent_t>> &vec) : ctx(c), v(&vec) {
+        if (ctx->cfg.timing) {
+            b = next_event(ctx);
+            cudaEventRecord(b, ctx->st);
+        }
+    }
+    ~Timed() {
+        if (b) {
+            cudaEvent_t e = next_event(ctx);
+            cudaEventRecord(e, ctx->st);
+            v->emplace_back(b, e);
+        }
+    }
+};
+
+void collect_times(skm_ctx *ctx) {
+    auto sum = [](std::vector<std::pair<cudaEvent_t, cudaEvent_t>> &v) {
+        double ms = 0;
+        for (auto &pr : v) {
+            float t = 0;
+            if (cudaEventElapsedTime(&t, pr.first, pr.second) == cudaSuccess) ms += t;
+        }
+        v.clear();
+        return ms;
+    };
+    ctx->stats.ms_score += sum(ctx->ev_score);
+    ctx->stats.ms_decide += sum(ctx->ev_decide);
+    ctx->stats.ms_update += sum(ctx->ev_update);
+    ctx->ev_next = 0;
+}
+
+// ---------------------------------------------------------------- helpers
+skm_status sync(skm_ctx *ctx) {
+    SKM_CUDA(cudaStreamSynchronize(ctx->st));
+    return SKM_OK;
+}
+
+skm_status read_counters(skm_ctx *ctx) {
+    SKM_CUDA(cudaMemcpyAsync(ctx->h_counters, ctx->counters.p, CNT_N * sizeof(int32_t),
+                             cudaMemcpyDeviceToHost, ctx->st));
+    SKM_CUDA(cudaMemcpyAsync(ctx->h_counters64, ctx->counters64.p, C64_N * sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost, ctx->st));
+    return sync(ctx);
+}
+
+skm_status reset_counters(skm_ctx *ctx) {
+    SKM_CUDA(cudaMemsetAsync(ctx->counters.p, 0, CNT_N * sizeof(int32_t), ctx->st));
+    SKM_CUDA(cudaMemsetAsync(ctx->counters64.p, 0, C64_N * sizeof(unsigned long long), ctx->st));
+    return SKM_OK;
+}
+
+struct DevCsr {
+    int64_t n;
+    int32_t d;
+    int64_t nnz;
+    const int64_t *row_ptr;
+    const int32_t *col;
+    const float *val;
+};
+
+// Host checks, staging (copy of host inputs), and device validation.
+skm_status stage_docs(skm_ctx *ctx, const skm_csr *docs, DevCsr &out) {
+    if (!docs) return fail(ctx, SKM_ERR_INVALID, "docs is NULL");
+    if (docs->n_docs < 1) return fail(ctx, SKM_ERR_INVALID, "n_docs must be >= 1");
+    if (docs->n_docs > INT32_MAX - 1) return fail(ctx, SKM_ERR_INVALID, "n_docs too large");
+    if (docs->n_terms < 1) return fail(ctx, SKM_ERR_INVALID, "n_terms must be >= 1");
+    if (docs->nnz < docs->n_docs) return fail(ctx, SKM_ERR_INVALID, "nnz < n_docs: empty rows");
+    if (!docs->row_ptr || !docs->col_idx || !docs->values)
+        return fail(ctx, SKM_ERR_INVALID, "NULL CSR array");
+    out.n = docs->n_docs;
+    out.d = docs->n_terms;
+    out.nnz = docs->nnz;
+    if (docs->on_device) {
+        int64_t ends[2];
+        SKM_CUDA(cudaMemcpyAsync(&ends[0], docs->row_ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->st));
+        SKM_CUDA(cudaMemcpyAsync(&ends[1], docs->row_ptr + docs->n_docs, sizeof(int64_t),
+                                 cudaMemcpyDeviceToHost, ctx->st));
+        SKM_TRY(sync(ctx));
+        if (ends[0] != 0 || ends[1] != docs->nnz)
+            return fail(ctx, SKM_ERR_INVALID, "row_ptr[0] must be 0 and row_ptr[n_docs] == nnz");
+        out.row_ptr = docs->row_ptr;
+        out.col = docs->col_idx;
+        out.val = docs->values;
+    } else {
+        if (docs->row_ptr[0] != 0 || docs->row_ptr[docs->n_docs] != docs->nnz)
+            return fail(ctx, SKM_ERR_INVALID, "row_ptr[0] must be 0 and row_ptr[n_docs] == nnz");
+        SKM_TRY(ensure(ctx, ctx->d_row_ptr, sizeof(int64_t) * (docs->n_docs + 1)));
+        SKM_TRY(ensure(ctx, ctx->d_col, sizeof(int32_t) * docs->nnz));
+        SKM_TRY(ensure(ctx, ctx->d_val, sizeof(float) * docs->nnz));
+        SKM_CUDA(cudaMemcpyAsync(ctx->d_row_ptr.p, docs->row_ptr, sizeof(int64_t) * (docs->n_docs + 1),
+                                 cudaMemcpyHostToDevice, ctx->st));
+        SKM_CUDA(cudaMemcpyAsync(ctx->d_col.p, docs->col_idx, sizeof(int32_t) * docs->nnz,
+                                 cudaMemcpyHostToDevice, ctx->st));
+        SKM_CUDA(cudaMemcpyAsync(ctx->d_val.p, docs->values, sizeof(float) * docs->nnz,
+                                 cudaMemcpyHostToDevice, ctx->st));
+        out.row_ptr = P<int64_t>(ctx->d_row_ptr);
+        out.col = P<int32_t>(ctx->d_col);
+        out.val = P<float>(ctx->d_val);
+    }
+    SKM_TRY(reset_counters(ctx));
+    SKM_CUDA(launch_validate(out.row_ptr, out.col, out.val, out.n, out.d,
+                             P<int32_t>(ctx->counters) + CNT_ERR, ctx->st));
+    ctx->stats.launches_total++;
+    SKM_TRY(read_counters(ctx));
+    const int e = ctx->h_counters[CNT_ERR];
+    if (e) {
+        std::string why;
+        if (e & 1) why += " column index out of range or not strictly increasing;";
+        if (e & 2) why += " value negative or not finite;";
+        if (e & 4) why += " empty row;";
+        if (e & 8) why += " row L2 norm not within 1e-5 of 1;";
+        if (e & 16) why += " row_ptr not monotone;";
+        return fail(ctx, SKM_ERR_INVALID, "invalid documents:%s", why.c_str());
+    }
+    return SKM_OK;
+}
+
+// Resident centroid matrices for vocabulary size d (contents zeroed when (re)allocated).
+skm_status ensure_centroids(skm_ctx *ctx, int32_t d, bool zero) {
+    const int32_t k = ctx->cfg.k;
+    const size_t n = (size_t)d * (size_t)ctx->ldc;
+    const bool fresh = ctx->d != d || !ctx->C32.p;
+    SKM_TRY(ensure(ctx, ctx->C32, n * sizeof(float)));
+    if (ctx->cfg.precision == SKM_BF16) SKM_TRY(ensure(ctx, ctx->C16, n * sizeof(__nv_bfloat16)));
+    SKM_TRY(ensure(ctx, ctx->CM, n * (ctx->cfg.precision == SKM_BF16 ? 2 : 4)));
+    SKM_TRY(ensure(ctx, ctx->norm_store, sizeof(double) * k));
+    if (fresh || zero) {
+        SKM_CUDA(cudaMemsetAsync(ctx->C32.p, 0, n * sizeof(float), ctx->st));
+        if (ctx->C16.p) SKM_CUDA(cudaMemsetAsync(ctx->C16.p, 0, n * sizeof(__nv_bfloat16), ctx->st));
+        SKM_CUDA(cudaMemsetAsync(ctx->CM.p, 0, n * (ctx->cfg.precision == SKM_BF16 ? 2 : 4), ctx->st));
+        SKM_CUDA(cudaMemsetAsync(ctx->norm_store.p, 0, sizeof(double) * k, ctx->st));
+    }
+    ctx->d = d;
+    return SKM_OK;
+}
+
+// Per-cluster buffers.
+skm_status ensure_cluster_bufs(skm_ctx *ctx) {
+    const int32_t k = ctx->cfg.k;
+    SKM_TRY(ensure(ctx, ctx->changed, k));
+    SKM_TRY(ensure(ctx, ctx->sizes, sizeof(int32_t) * k));
+    SKM_TRY(ensure(ctx, ctx->moved, sizeof(int32_t) * k));
+    SKM_TRY(ensure(ctx, ctx->pos_in_m, sizeof(int32_t) * k));
+    SKM_TRY(ensure(ctx, ctx->normsq, sizeof(double) * k));
+    SKM_TRY(ensure(ctx, ctx->inv_norm, sizeof(double) * k));
+    SKM_TRY(ensure(ctx, ctx->dot, sizeof(double) * k));
+    SKM_TRY(ensure(ctx, ctx->shift, sizeof(double) * k));
+    return SKM_OK;
+}
+
+// Per-document buffers for n documents.
+skm_status ensure_doc_bufs(skm_ctx *ctx, int64_t n) {
+    const int32_t k = ctx->cfg.k;
+    const int64_t n_slices = (k + ctx->slice - 1) / ctx->slice;
+    SKM_TRY(ensure(ctx, ctx->abuf[0], sizeof(int32_t) * n));
+    SKM_TRY(ensure(ctx, ctx->abuf[1], sizeof(int32_t) * n));
+    SKM_TRY(ensure(ctx, ctx->s_state, sizeof(float) * n));
+    SKM_TRY(ensure(ctx, ctx->r_state, sizeof(float) * n));
+    SKM_TRY(ensure(ctx, ctx->clean, n));
+    SKM_TRY(ensure(ctx, ctx->mdoc, sizeof(int32_t) * n));
+    SKM_TRY(ensure(ctx, ctx->part_s, sizeof(float) * n * n_slices * TOPT));
+    SKM_TRY(ensure(ctx, ctx->part_j, sizeof(int32_t) * n * n_slices * TOPT));
+    SKM_TRY(ensure(ctx, ctx->list_a, sizeof(int32_t) * n));
+    SKM_TRY(ensure(ctx, ctx->list_b, sizeof(int32_t) * n));
+    SKM_TRY(ensure(ctx, ctx->rs_doc, sizeof(int32_t) * n));
+    SKM_TRY(ensure(ctx, ctx->rs_cand, sizeof(int32_t) * n * TOPT));
+    SKM_TRY(ensure(ctx, ctx->refull, sizeof(int32_t) * n));
+    SKM_TRY(ensure(ctx, ctx->full64, sizeof(int32_t) * n));
+    return SKM_OK;
+}
+
+// Term-major postings of the staged documents and the update work list.
+struct Postings {
+    int32_t n_chunks = 0;
+    double scale = 0;
+    int64_t d_eff = 0;   // terms with at least one posting
+};
+
+skm_status build_postings(skm_ctx *ctx, const DevCsr &dc, Postings &pg) {
+    const int32_t d = dc.d;
+    SKM_TRY(ensure(ctx, ctx->tcount, sizeof(int32_t) * (d + 1)));
+    SKM_TRY(ensure(ctx, ctx->col_ptr, sizeof(int64_t) * (d + 1)));
+    SKM_TRY(ensure(ctx, ctx->row_idx, sizeof(int32_t) * dc.nnz));
+    SKM_TRY(ensure(ctx, ctx->cval, sizeof(float) * dc.nnz));
+    SKM_CUDA(cudaMemsetAsync(ctx->tcount.p, 0, sizeof(int32_t) * (d + 1), ctx->st));
+    SKM_CUDA(launch_term_count(dc.col, dc.nnz, P<int32_t>(ctx->tcount), ctx->st));
+    ctx->stats.launches_total++;
+    std::vector<int32_t> cnt(d);
+    SKM_CUDA(cudaMemcpyAsync(cnt.data(), ctx->tcount.p, sizeof(int32_t) * d, cudaMemcpyDeviceToHost, ctx->st));
+    SKM_TRY(sync(ctx));
+    std::vector<int64_t> cp(d + 1);
+    cp[0] = 0;
+    int64_t max_df = 1;
+    pg.d_eff = 0;
+    for (int32_t t = 0; t < d; ++t) {
+        cp[t + 1] = cp[t] + cnt[t];
+        max_df = std::max<int64_t>(max_df, cnt[t]);
+        pg.d_eff += cnt[t] > 0;
+    }
+    // Fixed point: every value is <= 1 + 1e-5, a sum has at most max_df terms.
+    int bits = 0;
+    while ((int64_t(1) << bits) < max_df + 1) ++bits;
+    const int F = 61 - bits;
+    pg.scale = std::ldexp(1.0, F);
+    // Work list: every term belongs to one chunk; chunks balance postings plus a per-term
+    // row cost, heavy terms alone.
+    const int64_t target = std::max<int64_t>(4096, (dc.nnz + (int64_t)d * 8) / 304 + 1);
+    std::vector<int32_t> t0, t1;
+    int64_t w = 0;
+    int32_t start = 0;
+    for (int32_t t = 0; t < d; ++t) {
+        w += cnt[t] + 8;
+        if (w >= target || t == d - 1) {
+            t0.push_back(start);
+            t1.push_back(t + 1);
+            start = t + 1;
+            w = 0;
+        }
+    }
+    pg.n_chunks = (int32_t)t0.size();
+    SKM_TRY(ensure(ctx, ctx->chunk_t0, sizeof(int32_t) * pg.n_chunks));
+    SKM_TRY(ensure(ctx, ctx->chunk_t1, sizeof(int32_t) * pg.n_chunks));
+    SKM_CUDA(cudaMemcpyAsync(ctx->col_ptr.p, cp.data(), sizeof(int64_t) * (d + 1), cudaMemcpyHostToDevice, ctx->st));
+    SKM_CUDA(cudaMemcpyAsync(ctx->chunk_t0.p, t0.data(), sizeof(int32_t) * pg.n_chunks, cudaMemcpyHostToDevice, ctx->st));
+    SKM_CUDA(cudaMemcpyAsync(ctx->chunk_t1.p, t1.data(), sizeof(int32_t) * pg.n_chunks, cudaMemcpyHostToDevice, ctx->st));
+    SKM_CUDA(cudaMemsetAsync(ctx->tcount.p, 0, sizeof(int32_t) * (d + 1), ctx->st));
+    SKM_CUDA(launch_csc_fill(dc.row_ptr, dc.col, dc.val, dc.n, P<int64_t>(ctx->col_ptr),
+                             P<int32_t>(ctx->tcount), P<int32_t>(ctx->row_idx), P<float>(ctx->cval), ctx->st));
+    ctx->stats.launches_total++;
+    // partial-sum buffers of the update passes
+    const int tile = update_tile();
+    const int32_t k = ctx->cfg.k;
+    const int64_t tiles = (k + tile - 1) / tile;
+    const size_t parts = (size_t)tiles * pg.n_chunks * tile;
+    SKM_TRY(ensure(ctx, ctx->part_norm, sizeof(double) * parts));
+    SKM_TRY(ensure(ctx, ctx->part_dot, sizeof(double) * parts));
+    SKM_TRY(ensure(ctx, ctx->part_shift, sizeof(double) * parts));
+    // the transient host vectors must outlive the async copies
+    SKM_TRY(sync(ctx));
+    return SKM_OK;
+}
+
+// Scoring pass over a document list (nullable = all) against all k or the moved list,
+// followed by the decision kernel.
+skm_status score_and_decide(skm_ctx *ctx, const DevCsr &dc, const int32_t *list, int32_t n_list,
+                            bool pruned, int32_t n_moved, const int32_t *a_old, int32_t *a_new,
+                            float *score_out) {
+    if (n_list <= 0) return SKM_OK;
+    const int32_t k = ctx->cfg.k;
+    const int prec = ctx->cfg.precision;
+    ScoreArgs sa{};
+    sa.row_ptr = dc.row_ptr;
+    sa.col = dc.col;
+    sa.val = dc.val;
+    sa.doc_list = list;
+    sa.n_list = n_list;
+    sa.ldc = ctx->ldc;
+    if (pruned) {
+        sa.C = ctx->CM.p;
+        sa.ncols = n_moved;
+        sa.col_ids = P<int32_t>(ctx->moved);
+    } else {
+        sa.C = prec == SKM_BF16 ? ctx->C16.p : ctx->C32.p;
+        sa.ncols = k;
+        sa.col_ids = nullptr;
+    }
+    sa.part_s = P<float>(ctx->part_s);
+    sa.part_j = P<int32_t>(ctx->part_j);
+    const int n_slices = (sa.ncols + ctx->slice - 1) / ctx->slice;
+    {
+        Timed tm(ctx, ctx->ev_score);
+        SKM_CUDA(launch_score(sa, prec, ctx->slice, ctx->st));
+    }
+    ctx->stats.launches_score++;
+    ctx->stats.launches_total++;
+    DecideArgs da{};
+    da.n_list = n_list;
+    da.doc_list = list;
+    da.n_slices = n_slices;
+    da.n_scored = sa.ncols;
+    da.part_s = sa.part_s;
+    da.part_j = sa.part_j;
+    da.row_ptr = dc.row_ptr;
+    da.precision = prec;
+    da.tau = (float)ctx->cfg.rescore_tau;
+    da.rescore = ctx->cfg.rescore;
+    da.pruned = pruned ? 1 : 0;
+    da.a_old = a_old;
+    da.a_new = a_new;
+    da.s_state = P<float>(ctx->s_state);
+    da.r_state = P<float>(ctx->r_state);
+    da.clean = P<uint8_t>(ctx->clean);
+    da.score_out = score_out;
+    da.counters = P<int32_t>(ctx->counters);
+    da.counters64 = P<unsigned long long>(ctx->counters64);
+    da.rs_doc = P<int32_t>(ctx->rs_doc);
+    da.rs_cand = P<int32_t>(ctx->rs_cand);
+    da.refull_doc = P<int32_t>(ctx->refull);
+    da.full64_doc = P<int32_t>(ctx->full64);
+    {
+        Timed tm(ctx, ctx->ev_decide);
+        SKM_CUDA(launch_decide(da, ctx->st));
+    }
+    ctx->stats.launches_total++;
+    return SKM_OK;
+}
+
+// Sum of nonzeros of listed documents (host copy of row_ptr needed): approximated on the
+// device side is not needed for correctness; the counters below use the list sizes.
+skm_status rescore_queues(skm_ctx *ctx, const DevCsr &dc, int32_t *a_new, float *score_out) {
+    SKM_TRY(read_counters(ctx));
+    const int n_rs = ctx->h_counters[CNT_RESCORE];
+    const int n_f64 = ctx->h_counters[CNT_FULL64];
+    if (n_rs > 0) {
+        RescoreArgs ra{};
+        ra.count = P<int32_t>(ctx->counters) + CNT_RESCORE;
+        ra.rs_doc = P<int32_t>(ctx->rs_doc);
+        ra.rs_cand = P<int32_t>(ctx->rs_cand);
+        ra.row_ptr = dc.row_ptr;
+        ra.col = dc.col;
+        ra.val = dc.val;
+        ra.C32 = P<float>(ctx->C32);
+        ra.ldc = ctx->ldc;
+        ra.a_new = a_new;
+        ra.score_out = score_out;
+        Timed tm(ctx, ctx->ev_decide);
+        SKM_CUDA(launch_rescore64(ra, n_rs, ctx->st));
+        ctx->stats.launches_total++;
+    }
+    if (n_f64 > 0) {
+        Full64Args fa{};
+        fa.count = P<int32_t>(ctx->counters) + CNT_FULL64;
+        fa.docs = P<int32_t>(ctx->full64);
+        fa.row_ptr = dc.row_ptr;
+        fa.col = dc.col;
+        fa.val = dc.val;
+        fa.C32 = P<float>(ctx->C32);
+        fa.ldc = ctx->ldc;
+        fa.k = ctx->cfg.k;
+        fa.a_new = a_new;
+        fa.score_out = score_out;
+        Timed tm(ctx, ctx->ev_decide);
+        SKM_CUDA(launch_full64(fa, n_f64, ctx->st));
+        ctx->stats.launches_total++;
+    }
+    ctx->stats.docs_rescored += n_rs;
+    ctx->stats.docs_rescored_full += n_f64;
+    return SKM_OK;
+}
+
+// One update step: changed flags, moved list, the two posting passes, objective and shift.
+// Returns the number of documents whose assignment changed and |M| through the counters.
+skm_status update_step(skm_ctx *ctx, const Postings &pg, const int32_t *a_new, const int32_t *a_old,
+                       int64_t n_docs, bool first, bool converged_check, bool *converged, int iter) {
+    const int32_t k = ctx->cfg.k;
+    Timed tm(ctx, ctx->ev_update);
+    SKM_CUDA(cudaMemsetAsync(ctx->changed.p, 0, k, ctx->st));
+    SKM_CUDA(cudaMemsetAsync(ctx->sizes.p, 0, sizeof(int32_t) * k, ctx->st));
+    SKM_CUDA(launch_changed(a_new, a_old, n_docs, first ? 1 : 0, P<uint8_t>(ctx->changed),
+                            P<int32_t>(ctx->sizes), k, P<int32_t>(ctx->counters), ctx->st));
+    SKM_CUDA(launch_compact_moved(P<uint8_t>(ctx->changed), k, P<int32_t>(ctx->moved),
+                                  P<int32_t>(ctx->pos_in_m), P<int32_t>(ctx->counters), ctx->st));
+    ctx->stats.launches_total += 2;
+    SKM_TRY(read_counters(ctx));
+    const int32_t n_changed_docs = ctx->h_counters[CNT_CHANGED];
+    const int32_t n_moved = ctx->h_counters[CNT_MOVED];
+    *converged = converged_check && !first && n_changed_docs == 0;
+    double *obj = P<double>(ctx->obj) + iter;
+    double *shf = P<double>(ctx->scal);
+    if (!*converged && n_moved > 0) {
+        UpdateArgs u{};
+        u.n_chunks = pg.n_chunks;
+        u.chunk_t0 = P<int32_t>(ctx->chunk_t0);
+        u.chunk_t1 = P<int32_t>(ctx->chunk_t1);
+        u.col_ptr = P<int64_t>(ctx->col_ptr);
+        u.row_idx = P<int32_t>(ctx->row_idx);
+        u.cval = P<float>(ctx->cval);
+        u.a = a_new;
+        u.mdoc = P<int32_t>(ctx->mdoc);
+        u.moved = P<int32_t>(ctx->moved);
+        u.pos_in_m = P<int32_t>(ctx->pos_in_m);
+        u.n_moved = n_moved;
+        u.sizes = P<int32_t>(ctx->sizes);
+        const int tile = update_tile();
+        const int tiles = (n_moved + tile - 1) / tile;
+        u.m_tile = ((n_moved + tiles - 1) / tiles + 31) & ~31;
+        u.scale = pg.scale;
+        u.part_norm = P<double>(ctx->part_norm);
+        u.inv_norm = P<double>(ctx->inv_norm);
+        u.C32 = P<float>(ctx->C32);
+        u.C16 = ctx->cfg.precision == SKM_BF16 ? P<__nv_bfloat16>(ctx->C16) : nullptr;
+        u.CM = ctx->CM.p;
+        u.precision = ctx->cfg.precision;
+        u.ldc = ctx->ldc;
+        u.part_dot = P<double>(ctx->part_dot);
+        u.part_shift = P<double>(ctx->part_shift);
+        SKM_CUDA(launch_mdoc(a_new, P<int32_t>(ctx->pos_in_m), n_docs, P<int32_t>(ctx->mdoc), ctx->st));
+        SKM_CUDA(launch_update_norm(u, ctx->st));
+        SKM_CUDA(launch_reduce_parts(u.part_norm, pg.n_chunks, u.m_tile, n_moved, P<double>(ctx->normsq), ctx->st));
+        SKM_CUDA(launch_inv_norm(P<double>(ctx->normsq), n_moved, P<double>(ctx->inv_norm), ctx->st));
+        SKM_CUDA(launch_update_write(u, ctx->st));
+        SKM_CUDA(launch_reduce_parts(u.part_dot, pg.n_chunks, u.m_tile, n_moved, P<double>(ctx->dot), ctx->st));
+        SKM_CUDA(launch_reduce_parts(u.part_shift, pg.n_chunks, u.m_tile, n_moved, P<double>(ctx->shift), ctx->st));
+        ctx->stats.launches_total += 7;
+    }
+    if (*converged) {
+        // no moved cluster: pos_in_m is -1 everywhere and the objective is sum_j ||S_j||
+    }
+    SKM_CUDA(launch_finish(P<int32_t>(ctx->pos_in_m), P<int32_t>(ctx->sizes), k, P<double>(ctx->dot),
+                           P<double>(ctx->normsq), P<double>(ctx->shift), P<double>(ctx->norm_store),
+                           obj, shf, ctx->st));
+    ctx->stats.launches_total++;
+    return SKM_OK;
+}
+
+skm_status common_checks(skm_ctx *ctx) {
+    if (!ctx) return SKM_ERR_INVALID;
+    ctx->err.clear();
+    return SKM_OK;
+}
+
+}  // namespace
+
+// =====================================================================================
+extern "C" {
+
+void skm_config_default(skm_config *cfg, int32_t k) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->k = k;
+    cfg->precision = SKM_FP32;
+    cfg->prune = SKM_PRUNE_NONE;
+    cfg->max_iter = 20;
+    cfg->shift_tol = -1.0;
+    cfg->rescore = 1;
+    cfg->rescore_tau = 0.0;
+}
+
+skm_status skm_create(const skm_config *cfg, skm_ctx **out) {
+    if (!cfg || !out) return SKM_ERR_INVALID;
+    *out = nullptr;
+    if (cfg->k < 1 || cfg->max_iter < 1 || (cfg->precision != SKM_FP32 && cfg->precision != SKM_BF16) ||
+        (cfg->prune != SKM_PRUNE_NONE && cfg->prune != SKM_PRUNE_NCC) || !(cfg->rescore_tau >= 0.0) ||
+        (cfg->alloc == nullptr) != (cfg->free == nullptr))
+        return SKM_ERR_INVALID;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
+        cudaGetLastError();
+        return SKM_ERR_CUDA;
+    }
+    DeviceGuard g(cfg->device);
+    skm_ctx *ctx = new skm_ctx();
+    ctx->cfg = *cfg;
+    ctx->st = (cudaStream_t)cfg->stream;
+    ctx->slice = slice_width(cfg->precision, cfg->k);
+    ctx->ldc = ((int64_t)cfg->k + ctx->slice - 1) / ctx->slice * ctx->slice;
+    if (ensure(ctx, ctx->counters, CNT_N * sizeof(int32_t)) != SKM_OK ||
+        ensure(ctx, ctx->counters64, C64_N * sizeof(unsigned long long)) != SKM_OK ||
+        cudaMallocHost(&ctx->h_counters64, C64_N * sizeof(unsigned long long)) != cudaSuccess ||
+        ensure(ctx, ctx->scal, 8 * sizeof(double)) != SKM_OK ||
+        cudaMallocHost(&ctx->h_counters, CNT_N * sizeof(int32_t)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_scal, 8 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        skm_destroy(ctx);
+        return SKM_ERR_OOM;
+    }
+    *out = ctx;
+    return SKM_OK;
+}
+
+skm_status skm_destroy(skm_ctx *ctx) {
+    if (!ctx) return SKM_OK;
+    DeviceGuard g(ctx->cfg.device);
+    cudaStreamSynchronize(ctx->st);
+    Buf *all[] = {&ctx->C32, &ctx->C16, &ctx->CM, &ctx->norm_store, &ctx->d_row_ptr, &ctx->d_col,
+                  &ctx->d_val, &ctx->col_ptr, &ctx->row_idx, &ctx->cval, &ctx->tcount, &ctx->chunk_t0,
+                  &ctx->chunk_t1, &ctx->abuf[0], &ctx->abuf[1], &ctx->s_state, &ctx->r_state,
+                  &ctx->clean, &ctx->mdoc, &ctx->part_s, &ctx->part_j, &ctx->list_a, &ctx->list_b, &ctx->rs_doc,
+                  &ctx->rs_cand, &ctx->refull, &ctx->full64, &ctx->changed, &ctx->sizes, &ctx->moved,
+                  &ctx->pos_in_m, &ctx->normsq, &ctx->inv_norm, &ctx->dot, &ctx->shift,
+                  &ctx->part_norm, &ctx->part_dot, &ctx->part_shift, &ctx->counters, &ctx->counters64, &ctx->scal,
+                  &ctx->obj, &ctx->init_ids};
+    for (Buf *b : all) release(ctx, *b);
+    if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
+    if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
+    if (ctx->h_counters64) cudaFreeHost(ctx->h_counters64);
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    delete ctx;
+    return SKM_OK;
+}
+
+const char *skm_last_error(const skm_ctx *ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
+
+int32_t skm_n_terms(const skm_ctx *ctx) { return ctx ? ctx->d : 0; }
+
+size_t skm_mem_used(const skm_ctx *ctx) { return ctx ? ctx->used : 0; }
+
+skm_status skm_get_stats(const skm_ctx *ctx, skm_stats *out) {
+    if (!ctx || !out) return SKM_ERR_INVALID;
+    *out = ctx->stats;
+    return SKM_OK;
+}
+
+skm_status skm_fit(skm_ctx *ctx, const skm_csr *docs, const int32_t *init_doc_ids, int32_t *assign_out,
+                   double *objective_out, int32_t *iters_out) {
+    SKM_TRY(common_checks(ctx));
+    DeviceGuard g(ctx->cfg.device);
+    const int32_t k = ctx->cfg.k;
+    if (!init_doc_ids || !assign_out) return fail(ctx, SKM_ERR_INVALID, "init_doc_ids and assign_out are required");
+    if (docs && docs->n_docs < k) return fail(ctx, SKM_ERR_INVALID, "k = %d exceeds n_docs = %lld", k, (long long)docs->n_docs);
+    {
+        std::vector<char> seen(docs ? (size_t)docs->n_docs : 0, 0);
+        for (int32_t j = 0; j < k && docs; ++j) {
+            const int32_t id = init_doc_ids[j];
+            if (id < 0 || id >= docs->n_docs) return fail(ctx, SKM_ERR_INVALID, "init id %d out of range", id);
+            if (seen[id]) return fail(ctx, SKM_ERR_INVALID, "init ids are not distinct (%d)", id);
+            seen[id] = 1;
+        }
+    }
+    ctx->stats = skm_stats{};
+    ctx->ev_score.clear();
+    ctx->ev_decide.clear();
+    ctx->ev_update.clear();
+    ctx->ev_next = 0;
+    DevCsr dc{};
+    SKM_TRY(stage_docs(ctx, docs, dc));
+    const int64_t N = dc.n;
+    SKM_TRY(ensure_centroids(ctx, dc.d, true));
+    SKM_TRY(ensure_cluster_bufs(ctx));
+    SKM_TRY(ensure_doc_bufs(ctx, N));
+    SKM_TRY(ensure(ctx, ctx->obj, sizeof(double) * ctx->cfg.max_iter));
+    SKM_TRY(ensure(ctx, ctx->init_ids, sizeof(int32_t) * k));
+    Postings pg;
+    SKM_TRY(build_postings(ctx, dc, pg));
+    SKM_CUDA(cudaMemcpyAsync(ctx->init_ids.p, init_doc_ids, sizeof(int32_t) * k, cudaMemcpyHostToDevice, ctx->st));
+    SKM_CUDA(launch_init_centroids(dc.row_ptr, dc.col, dc.val, P<int32_t>(ctx->init_ids), k, P<float>(ctx->C32),
+                                   ctx->cfg.precision == SKM_BF16 ? P<__nv_bfloat16>(ctx->C16) : nullptr,
+                                   ctx->ldc, ctx->st));
+    ctx->stats.launches_total++;
+    SKM_CUDA(cudaMemsetAsync(ctx->clean.p, 0, N, ctx->st));
+    SKM_CUDA(cudaMemsetAsync(ctx->changed.p, 1, k, ctx->st));
+
+    const bool prune = ctx->cfg.prune == SKM_PRUNE_NCC;
+    int32_t n_moved_prev = k;
+    int32_t it = 0;
+    int cur = 0;
+    for (int32_t t = 1; t <= ctx->cfg.max_iter; ++t) {
+        it = t;
+        const bool first = t == 1;
+        int32_t *a_old = P<int32_t>(ctx->abuf[cur ^ 1]);
+        int32_t *a_new = P<int32_t>(ctx->abuf[cur]);
+        SKM_TRY(reset_counters(ctx));
+        int32_t n_pruned = 0, n_full = (int32_t)N;
+        const int32_t *full_list = nullptr;
+        if (prune && !first) {
+            PartitionArgs pa{};
+            pa.n_docs = N;
+            pa.prune = 1;
+            pa.clean = P<uint8_t>(ctx->clean);
+            pa.changed = P<uint8_t>(ctx->changed);
+            pa.a_old = a_old;
+            pa.row_ptr = dc.row_ptr;
+            pa.counters = P<int32_t>(ctx->counters);
+            pa.counters64 = P<unsigned long long>(ctx->counters64);
+            pa.pruned_list = P<int32_t>(ctx->list_a);
+            pa.full_list = P<int32_t>(ctx->list_b);
+            SKM_CUDA(launch_partition(pa, ctx->st));
+            ctx->stats.launches_total++;
+            SKM_TRY(read_counters(ctx));
+            n_pruned = ctx->h_counters[CNT_PRUNED];
+            n_full = ctx->h_counters[CNT_FULL];
+            full_list = P<int32_t>(ctx->list_b);
+        }
+        // pruned documents keep a_old unless the decision moves them; copy it first
+        if (n_pruned > 0) SKM_CUDA(cudaMemcpyAsync(a_new, a_old, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, ctx->st));
+        SKM_TRY(score_and_decide(ctx, dc, full_list, n_full, false, k, a_old, a_new, nullptr));
+        SKM_TRY(score_and_decide(ctx, dc, P<int32_t>(ctx->list_a), n_pruned, true, n_moved_prev, a_old, a_new, nullptr));
+        ctx->stats.docs_full += n_full;
+        ctx->stats.docs_pruned += n_pruned;
+        ctx->stats.moved_total += n_pruned > 0 ? n_moved_prev : 0;
+        ctx->stats.sims += (int64_t)n_full * k + (int64_t)n_pruned * n_moved_prev;
+        SKM_TRY(read_counters(ctx));
+        const int64_t nnz_pruned = n_pruned > 0 ? (int64_t)ctx->h_counters64[C64_NNZ_PRUNED] : 0;
+        const int64_t nnz_full = dc.nnz - nnz_pruned;
+        const int32_t n_refull = ctx->h_counters[CNT_REFULL];
+        const int64_t nnz_refull = n_refull > 0 ? (int64_t)ctx->h_counters64[C64_NNZ_REFULL] : 0;
+        if (n_refull > 0) {
+            SKM_TRY(score_and_decide(ctx, dc, P<int32_t>(ctx->refull), n_refull, false, k, a_old, a_new, nullptr));
+            ctx->stats.sims += (int64_t)n_refull * k;
+            ctx->stats.docs_full += n_refull;
+        }
+        // algorithmic work of the scoring passes: one FMA per (nonzero, scored centroid);
+        // bytes = CSR entries and per-document state of every scored document, plus each
+        // needed centroid element once (rows of present terms x scored columns)
+        const int64_t elt = ctx->cfg.precision == SKM_BF16 ? 2 : 4;
+        ctx->stats.fmas += nnz_full * k + nnz_pruned * n_moved_prev + nnz_refull * k;
+        const int32_t cols_needed = (n_full > 0 || n_refull > 0) ? k : n_moved_prev;
+        ctx->stats.bytes += 8 * (dc.nnz + nnz_refull) + 20 * (N + n_refull) + pg.d_eff * cols_needed * elt;
+        SKM_TRY(rescore_queues(ctx, dc, a_new, nullptr));
+        bool converged = false;
+        SKM_TRY(update_step(ctx, pg, a_new, a_old, N, first, true, &converged, t - 1));
+        n_moved_prev = ctx->h_counters[CNT_MOVED];
+        cur ^= 1;
+        if (converged) break;
+        if (ctx->cfg.shift_tol >= 0.0) {
+            SKM_CUDA(cudaMemcpyAsync(ctx->h_scal, ctx->scal.p, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+            SKM_TRY(sync(ctx));
+            if (ctx->h_scal[0] < ctx->cfg.shift_tol) break;
+        }
+    }
+    // the last decided assignment is in abuf[cur ^ 1]
+    int32_t *a_fin = P<int32_t>(ctx->abuf[cur ^ 1]);
+    SKM_CUDA(cudaMemcpyAsync(assign_out, a_fin, sizeof(int32_t) * N,
+                             docs->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->st));
+    if (objective_out)
+        SKM_CUDA(cudaMemcpyAsync(objective_out, ctx->obj.p, sizeof(double) * it, cudaMemcpyDeviceToHost, ctx->st));
+    SKM_TRY(sync(ctx));
+    collect_times(ctx);
+    ctx->stats.iters = it;
+    if (iters_out) *iters_out = it;
+    return SKM_OK;
+}
+
+skm_status skm_assign(skm_ctx *ctx, const skm_csr *docs, int32_t *assign_out, float *score_out) {
+    SKM_TRY(common_checks(ctx));
+    DeviceGuard g(ctx->cfg.device);
+    if (!assign_out) return fail(ctx, SKM_ERR_INVALID, "assign_out is required");
+    if (ctx->d == 0 || !ctx->C32.p) return fail(ctx, SKM_ERR_STATE, "no resident centroids");
+    if (docs && docs->n_terms != ctx->d)
+        return fail(ctx, SKM_ERR_INVALID, "n_terms %d differs from the resident vocabulary %d", docs->n_terms, ctx->d);
+    ctx->stats = skm_stats{};
+    ctx->ev_next = 0;
+    DevCsr dc{};
+    SKM_TRY(stage_docs(ctx, docs, dc));
+    const int64_t N = dc.n;
+    SKM_TRY(ensure_doc_bufs(ctx, N));
+    int32_t *a_new = P<int32_t>(ctx->abuf[0]);
+    SKM_TRY(reset_counters(ctx));
+    // scores go straight to a device output, or through a temporary for a host output
+    float *score_dev = nullptr;
+    Buf tmp_score;
+    if (score_out && !docs->on_device) {
+        SKM_TRY(ensure(ctx, tmp_score, sizeof(float) * N));
+        score_dev = P<float>(tmp_score);
+    } else {
+        score_dev = score_out;
+    }
+    skm_status s = score_and_decide(ctx, dc, nullptr, (int32_t)N, false, ctx->cfg.k, nullptr, a_new, score_dev);
+    if (s == SKM_OK) s = rescore_queues(ctx, dc, a_new, score_dev);
+    if (s == SKM_OK) {
+        const cudaMemcpyKind kind = docs->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        cudaError_t e = cudaMemcpyAsync(assign_out, a_new, sizeof(int32_t) * N, kind, ctx->st);
+        if (e == cudaSuccess && score_out && !docs->on_device)
+            e = cudaMemcpyAsync(score_out, score_dev, sizeof(float) * N, cudaMemcpyDeviceToHost, ctx->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+        if (e != cudaSuccess) s = fail(ctx, SKM_ERR_CUDA, "copy-out failed: %s", cudaGetErrorString(e));
+    }
+    release(ctx, tmp_score);
+    collect_times(ctx);
+    ctx->stats.docs_full = N;
+    ctx->stats.sims = N * (int64_t)ctx->cfg.k;
+    ctx->stats.fmas = dc.nnz * (int64_t)ctx->cfg.k;
+    ctx->stats.bytes = 8 * dc.nnz + 20 * N +
+                       (int64_t)ctx->d * ctx->cfg.k * (ctx->cfg.precision == SKM_BF16 ? 2 : 4);
+    ctx->stats.iters = 1;
+    return s;
+}
+
+skm_status skm_update(skm_ctx *ctx, const skm_csr *docs, const int32_t *assign, int32_t *n_changed_out) {
+    SKM_TRY(common_checks(ctx));
+    DeviceGuard g(ctx->cfg.device);
+    if (!assign) return fail(ctx, SKM_ERR_INVALID, "assign is required");
+    DevCsr dc{};
+    SKM_TRY(stage_docs(ctx, docs, dc));
+    const int64_t N = dc.n;
+    const int32_t k = ctx->cfg.k;
+    // assignments: range check on the host copy
+    std::vector<int32_t> ha;
+    const int32_t *a_dev = nullptr;
+    SKM_TRY(ensure_doc_bufs(ctx, N));
+    if (docs->on_device) {
+        ha.resize(N);
+        SKM_CUDA(cudaMemcpyAsync(ha.data(), assign, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, ctx->st));
+        SKM_TRY(sync(ctx));
+        a_dev = assign;
+    } else {
+        ha.assign(assign, assign + N);
+        SKM_CUDA(cudaMemcpyAsync(ctx->abuf[0].p, assign, sizeof(int32_t) * N, cudaMemcpyHostToDevice, ctx->st));
+        a_dev = P<int32_t>(ctx->abuf[0]);
+    }
+    for (int64_t i = 0; i < N; ++i)
+        if (ha[i] < 0 || ha[i] >= k) return fail(ctx, SKM_ERR_INVALID, "assign[%lld] = %d out of range", (long long)i, ha[i]);
+    const bool fresh = ctx->d != dc.d;
+    SKM_TRY(ensure_centroids(ctx, dc.d, fresh));
+    SKM_TRY(ensure_cluster_bufs(ctx));
+    SKM_TRY(ensure(ctx, ctx->obj, sizeof(double) * std::max(1, ctx->cfg.max_iter)));
+    Postings pg;
+    SKM_TRY(build_postings(ctx, dc, pg));
+    SKM_TRY(reset_counters(ctx));
+    bool conv = false;
+    SKM_TRY(update_step(ctx, pg, a_dev, nullptr, N, true, false, &conv, 0));
+    SKM_TRY(sync(ctx));
+    collect_times(ctx);
+    if (n_changed_out) *n_changed_out = ctx->h_counters[CNT_MOVED];
+    return SKM_OK;
+}
+
+skm_status skm_set_centroids(skm_ctx *ctx, int32_t n_terms, const float *centroids, int32_t on_device) {
+    SKM_TRY(common_checks(ctx));
+    DeviceGuard g(ctx->cfg.device);
+    if (n_terms < 1 || !centroids) return fail(ctx, SKM_ERR_INVALID, "n_terms >= 1 and centroids required");
+    const int32_t k = ctx->cfg.k;
+    SKM_TRY(ensure_centroids(ctx, n_terms, true));
+    SKM_CUDA(cudaMemcpy2DAsync(ctx->C32.p, sizeof(float) * ctx->ldc, centroids, sizeof(float) * k,
+                               sizeof(float) * k, n_terms,
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->st));
+    if (ctx->cfg.precision == SKM_BF16) {
+        SKM_CUDA(launch_to_bf16(P<float>(ctx->C32), P<__nv_bfloat16>(ctx->C16), (int64_t)n_terms * ctx->ldc, ctx->st));
+        ctx->stats.launches_total++;
+    }
+    return sync(ctx);
+}
+
+skm_status skm_get_centroids(skm_ctx *ctx, float *out, int32_t on_device) {
+    SKM_TRY(common_checks(ctx));
+    DeviceGuard g(ctx->cfg.device);
+    if (!out) return fail(ctx, SKM_ERR_INVALID, "output is NULL");
+    if (ctx->d == 0 || !ctx->C32.p) return fail(ctx, SKM_ERR_STATE, "no resident centroids");
+    const int32_t k = ctx->cfg.k;
+    SKM_CUDA(cudaMemcpy2DAsync(out, sizeof(float) * k, ctx->C32.p, sizeof(float) * ctx->ldc, sizeof(float) * k,
+                               ctx->d, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->st));
+    return sync(ctx);
+}
+
+}  // extern "C"

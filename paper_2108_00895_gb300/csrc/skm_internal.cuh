@@ -1,0 +1,104 @@
+// Internal declarations shared by the CUDA translation units of libskm.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace skm {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int TOPT = 4;   // candidates kept per (document, slice) and per document
+
+// ---------------------------------------------------------------- candidate order
+// (s, j) is better than (s', j') when s > s', or s == s' and j < j'
+// (argmax ties go to the lowest centroid index).
+__device__ __forceinline__ bool better(float s, int j, float s2, int j2) {
+    return s > s2 || (s == s2 && j < j2);
+}
+__device__ __forceinline__ bool better64(double s, int j, double s2, int j2) {
+    return s > s2 || (s == s2 && j < j2);
+}
+
+// Insert (s, j) into a list kept sorted best-first (length TOPT, registers).
+__device__ __forceinline__ void topt_insert(float (&ls)[TOPT], int (&lj)[TOPT], float s, int j) {
+    if (!better(s, j, ls[TOPT - 1], lj[TOPT - 1])) return;
+    ls[TOPT - 1] = s;
+    lj[TOPT - 1] = j;
+#pragma unroll
+    for (int q = TOPT - 1; q > 0; --q) {
+        if (better(ls[q], lj[q], ls[q - 1], lj[q - 1])) {
+            float ts = ls[q]; ls[q] = ls[q - 1]; ls[q - 1] = ts;
+            int tj = lj[q]; lj[q] = lj[q - 1]; lj[q - 1] = tj;
+        }
+    }
+}
+
+// Keep the best TOPT of two best-first lists a and b (result in a). Bitonic merge with
+// static register indices: c[q] = better of a[q] and b[TOPT-1-q] holds the best TOPT as
+// a bitonic sequence, which two half-cleaner stages then sort.
+__device__ __forceinline__ void topt_merge2(float (&as)[TOPT], int (&aj)[TOPT],
+                                            const float (&bs)[TOPT], const int (&bj)[TOPT]) {
+    static_assert(TOPT == 4, "bitonic network below is written for 4 entries");
+#pragma unroll
+    for (int q = 0; q < TOPT; ++q) {
+        if (!better(as[q], aj[q], bs[TOPT - 1 - q], bj[TOPT - 1 - q])) {
+            as[q] = bs[TOPT - 1 - q];
+            aj[q] = bj[TOPT - 1 - q];
+        }
+    }
+#define SKM_CSWAP(x, y)                                                      \
+    if (better(as[y], aj[y], as[x], aj[x])) {                                \
+        float ts = as[x]; as[x] = as[y]; as[y] = ts;                         \
+        int tj = aj[x]; aj[x] = aj[y]; aj[y] = tj;                           \
+    }
+    SKM_CSWAP(0, 2) SKM_CSWAP(1, 3) SKM_CSWAP(0, 1) SKM_CSWAP(2, 3)
+#undef SKM_CSWAP
+}
+
+// Merge the lists of all 32 lanes (butterfly); every lane ends with the warp's best TOPT.
+__device__ __forceinline__ void topt_warp_merge(float (&ls)[TOPT], int (&lj)[TOPT]) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        float os[TOPT];
+        int oj[TOPT];
+#pragma unroll
+        for (int q = 0; q < TOPT; ++q) {
+            os[q] = __shfl_xor_sync(FULL, ls[q], off);
+            oj[q] = __shfl_xor_sync(FULL, lj[q], off);
+        }
+        topt_merge2(ls, lj, os, oj);
+    }
+}
+
+// ---------------------------------------------------------------- bf16 widening
+__device__ __forceinline__ float bf16lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+
+// Read-only, streaming 16-byte load.
+__device__ __forceinline__ uint4 ldg16(const void *p) {
+    return __ldg(reinterpret_cast<const uint4 *>(p));
+}
+
+// ---------------------------------------------------------------- kernel entry points
+// Scoring: one warp per (document, slice of KS columns). Writes the slice's best TOPT
+// (score, centroid id) to part[(slice * n_list + pos) * TOPT + q].
+struct ScoreArgs {
+    const int64_t *row_ptr;
+    const int32_t *col;
+    const float *val;
+    const int32_t *doc_list;   // nullable: position pos scores document doc_list[pos]
+    int32_t n_list;
+    const void *C;             // term-major centroid matrix, row stride ldc elements
+    int64_t ldc;
+    int32_t ncols;             // valid columns (scores of columns >= ncols are ignored)
+    const int32_t *col_ids;    // nullable: column -> centroid id (compacted matrices)
+    float *part_s;
+    int32_t *part_j;
+};
+
+// Launch helpers (defined in assign.cu). Return cudaSuccess or the launch error.
+cudaError_t launch_score(const ScoreArgs &a, int precision, int slice_cols, cudaStream_t st);
+int slice_width(int precision, int k);   // KS for the scoring kernel
+
+}  // namespace skm

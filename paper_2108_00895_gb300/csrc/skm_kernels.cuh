@@ -1,0 +1,169 @@
+// Argument blocks and launch helpers of the libskm kernels (internal).
+#pragma once
+
+#include "skm_internal.cuh"
+
+namespace skm {
+
+// Device counters, one int32 each (reset per step by the host).
+enum {
+    CNT_PRUNED = 0,   // documents in the pruned class
+    CNT_FULL = 1,     // documents in the full class
+    CNT_RESCORE = 2,  // documents queued for FP64 rescoring of a candidate list
+    CNT_REFULL = 3,   // pruned documents sent back to full scoring
+    CNT_FULL64 = 4,   // documents queued for FP64 scoring against all k
+    CNT_CHANGED = 5,  // documents whose assignment changed in this step
+    CNT_MOVED = 6,    // centroids in the moved list
+    CNT_ERR = 7,      // validation error flags (bitmask)
+    CNT_N = 8
+};
+// 64-bit device counters (nonzeros of listed documents, for the work counts).
+enum { C64_NNZ_PRUNED = 0, C64_NNZ_REFULL = 1, C64_N = 2 };
+
+struct DecideArgs {
+    int32_t n_list;
+    const int32_t *doc_list;   // nullable: identity
+    int32_t n_slices;
+    int32_t n_scored;          // size of the scored set (k, or the moved-list length)
+    const float *part_s;
+    const int32_t *part_j;
+    const int64_t *row_ptr;
+    int precision;             // 0 FP32, 1 BF16 (error bound of the scored copy)
+    float tau;
+    int rescore;
+    int pruned;                // 1: documents of the pruned class (fold in stored state)
+    const int32_t *a_old;      // previous assignment (pruned class)
+    int32_t *a_new;
+    float *s_state;            // scoring-pass score of the assigned centroid
+    float *r_state;            // upper bound on the scoring-pass score of any other centroid
+    uint8_t *clean;            // 1: last decision needed no rescoring
+    float *score_out;          // nullable
+    int32_t *counters;
+    unsigned long long *counters64;
+    int32_t *rs_doc;           // rescore queue: document ids
+    int32_t *rs_cand;          // rescore queue: TOPT candidates each (-1 = none)
+    int32_t *refull_doc;
+    int32_t *full64_doc;
+};
+
+struct RescoreArgs {
+    const int32_t *count;
+    const int32_t *rs_doc;
+    const int32_t *rs_cand;
+    const int64_t *row_ptr;
+    const int32_t *col;
+    const float *val;
+    const float *C32;
+    int64_t ldc;
+    int32_t *a_new;
+    float *score_out;
+};
+
+struct Full64Args {
+    const int32_t *count;
+    const int32_t *docs;
+    const int64_t *row_ptr;
+    const int32_t *col;
+    const float *val;
+    const float *C32;
+    int64_t ldc;
+    int32_t k;
+    int32_t *a_new;
+    float *score_out;
+};
+
+struct PartitionArgs {
+    int64_t n_docs;
+    int prune;
+    const uint8_t *clean;
+    const uint8_t *changed;
+    const int32_t *a_old;
+    const int64_t *row_ptr;
+    int32_t *counters;
+    unsigned long long *counters64;
+    int32_t *pruned_list;
+    int32_t *full_list;
+};
+
+cudaError_t launch_decide(const DecideArgs &a, cudaStream_t st);
+cudaError_t launch_rescore64(const RescoreArgs &a, int n_max, cudaStream_t st);
+cudaError_t launch_full64(const Full64Args &a, int n_max, cudaStream_t st);
+cudaError_t launch_partition(const PartitionArgs &a, cudaStream_t st);
+
+// ---------------------------------------------------------------- update (update.cu)
+// Input validation of a CSR collection; sets bits in *err:
+//   1 column out of range or not strictly increasing, 2 value negative or not finite,
+//   4 empty row, 8 row norm not within 1e-5 of 1, 16 row_ptr not monotone.
+cudaError_t launch_validate(const int64_t *row_ptr, const int32_t *col, const float *val,
+                            int64_t n_docs, int32_t n_terms, int32_t *err, cudaStream_t st);
+
+// Term-major transpose (CSC) of the collection: counts per term, then a fill.
+cudaError_t launch_term_count(const int32_t *col, int64_t nnz, int32_t *cnt, cudaStream_t st);
+cudaError_t launch_csc_fill(const int64_t *row_ptr, const int32_t *col, const float *val,
+                            int64_t n_docs, const int64_t *col_ptr, int32_t *fill,
+                            int32_t *row_idx, float *cval, cudaStream_t st);
+
+// Initial centroids c_j = x_{ids[j]} (the matrices must be zero beforehand).
+cudaError_t launch_init_centroids(const int64_t *row_ptr, const int32_t *col, const float *val,
+                                  const int32_t *ids, int32_t k, float *C32, __nv_bfloat16 *C16,
+                                  int64_t ldc, cudaStream_t st);
+
+// Per step: changed-cluster flags from the two assignments, cluster sizes, changed count.
+cudaError_t launch_changed(const int32_t *a_new, const int32_t *a_old, int64_t n_docs, int first,
+                           uint8_t *changed, int32_t *sizes, int32_t k, int32_t *counters,
+                           cudaStream_t st);
+// Moved list M (ascending), pos_in_M (-1 if not moved), |M| into counters[CNT_MOVED].
+cudaError_t launch_compact_moved(const uint8_t *changed, int32_t k, int32_t *moved,
+                                 int32_t *pos_in_m, int32_t *counters, cudaStream_t st);
+
+struct UpdateArgs {
+    // work list: chunk c covers terms [chunk_t0[c], chunk_t1[c])
+    int32_t n_chunks;
+    const int32_t *chunk_t0;
+    const int32_t *chunk_t1;
+    const int64_t *col_ptr;
+    const int32_t *row_idx;
+    const float *cval;
+    const int32_t *a;          // assignment of this step
+    const int32_t *mdoc;       // per document: moved-list position of its cluster, or -1
+    const int32_t *moved;      // M
+    const int32_t *pos_in_m;
+    int32_t n_moved;
+    const int32_t *sizes;      // members per cluster
+    int32_t m_tile;            // moved entries per tile (grid.y = tiles)
+    double scale;              // fixed-point scale 2^F
+    // norm pass output: part[(tile * n_chunks + c) * m_tile + m]
+    double *part_norm;
+    // write pass
+    const double *inv_norm;    // [n_moved]
+    float *C32;
+    __nv_bfloat16 *C16;        // nullable (FP32 mode)
+    void *CM;                  // compacted moved matrix (precision of the scored copy)
+    int precision;
+    int64_t ldc;
+    double *part_dot;          // sum_t S(t,j) * c_old(t,j)   (objective)
+    double *part_shift;        // sum_t (c_new - c_old)^2      (stop rule)
+};
+cudaError_t launch_update_norm(const UpdateArgs &u, cudaStream_t st);
+cudaError_t launch_update_write(const UpdateArgs &u, cudaStream_t st);
+int update_tile();   // largest moved-list tile of one update block
+cudaError_t launch_mdoc(const int32_t *a, const int32_t *pos_in_m, int64_t n, int32_t *mdoc,
+                        cudaStream_t st);
+// Column sums over chunks in chunk order: out[m] = sum_c part[(tile*n_chunks + c)*m_tile + m].
+cudaError_t launch_reduce_parts(const double *part, int32_t n_chunks, int32_t m_tile,
+                                int32_t n_moved, double *out, cudaStream_t st);
+// inv_norm[m] = 1 / sqrt(normsq[m]) (0 for an empty sum).
+cudaError_t launch_inv_norm(const double *normsq, int32_t n_moved, double *inv_norm,
+                            cudaStream_t st);
+// Objective and shift of one step (single block, fixed order). See update.cu.
+cudaError_t launch_finish(const int32_t *pos_in_m, const int32_t *sizes, int32_t k,
+                          const double *dot, const double *normsq, const double *shift,
+                          double *norm_store, double *obj_out, double *shift_out,
+                          cudaStream_t st);
+// FP32 -> BF16 (round to nearest even) of a d x ldc matrix.
+cudaError_t launch_to_bf16(const float *C32, __nv_bfloat16 *C16, int64_t n, cudaStream_t st);
+// Copy a dense term-major d x k matrix into a padded one (and back).
+cudaError_t launch_pad_copy(const float *src, int64_t src_ld, float *dst, int64_t dst_ld,
+                            int32_t rows, int32_t cols, cudaStream_t st);
+
+}  // namespace skm

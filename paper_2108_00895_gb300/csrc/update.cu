@@ -1,0 +1,492 @@
+// Centroid update (Sec. 2 of the paper): c_j = S_j / ||S_j||, S_j the sum of the member
+// documents of cluster j, computed only for clusters whose membership changed (the
+// non-changing-clusters reading of Sec. 3.1: an unchanged cluster keeps its centroid
+// bit for bit).
+//
+// Layout: the collection is transposed once per fit into term-major postings (CSC). For
+// each term t the postings are bucketed by the cluster of their document; each bucket's
+// sum S(t, j) is accumulated exactly as a 64-bit fixed-point integer (value * 2^F, F chosen
+// so no sum can overflow), so the result does not depend on the order in which threads add
+// their postings: the update is deterministic without a sort of the postings. The rows of
+// the term-major centroid matrix are then written with coalesced stores.
+//
+// Two passes over the postings: the first accumulates ||S_j||^2 (FP64, fixed term order
+// per chunk, chunks reduced in order), the second writes c = S / ||S|| into the FP32
+// master, the BF16 copy and the compacted moved-centroid matrix, and accumulates the
+// objective term S_j . c_j(old) and the squared shift ||c_j(new) - c_j(old)||^2.
+#include "skm_kernels.cuh"
+
+namespace skm {
+
+// ------------------------------------------------------------------------------------
+// Validation: one warp per row.
+// ------------------------------------------------------------------------------------
+__global__ void k_validate(const int64_t *row_ptr, const int32_t *col, const float *val,
+                           int64_t n_docs, int32_t n_terms, int32_t *err) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n_docs) return;
+    const int64_t beg = row_ptr[i], end = row_ptr[i + 1];
+    int e = 0;
+    if (end < beg) e |= 16;
+    if (end == beg) e |= 4;
+    double ss = 0.0;
+    if (end > beg) {
+        for (int64_t p = beg + lane; p < end; p += 32) {
+            const int32_t t = col[p];
+            if (t < 0 || t >= n_terms) e |= 1;
+            if (p > beg && col[p - 1] >= t) e |= 1;
+            const float v = val[p];
+            if (!(v >= 0.f) || !isfinite(v)) e |= 2;
+            ss += (double)v * (double)v;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) ss += __shfl_xor_sync(FULL, ss, off);
+        if (lane == 0 && !(fabs(sqrt(ss) - 1.0) <= 1e-5)) e |= 8;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) e |= __shfl_xor_sync(FULL, e, off);
+    if (lane == 0 && e) atomicOr(err, e);
+}
+
+cudaError_t launch_validate(const int64_t *row_ptr, const int32_t *col, const float *val,
+                            int64_t n_docs, int32_t n_terms, int32_t *err, cudaStream_t st) {
+    if (n_docs <= 0) return cudaSuccess;
+    const int64_t threads = n_docs * 32;
+    k_validate<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(row_ptr, col, val, n_docs,
+                                                                  n_terms, err);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// Transpose to term-major postings.
+// ------------------------------------------------------------------------------------
+__global__ void k_term_count(const int32_t *col, int64_t nnz, int32_t *cnt) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz;
+         p += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(cnt + col[p], 1);
+}
+
+cudaError_t launch_term_count(const int32_t *col, int64_t nnz, int32_t *cnt, cudaStream_t st) {
+    if (nnz <= 0) return cudaSuccess;
+    const int64_t blocks = min((int64_t)152 * 16, (nnz + 255) / 256);
+    k_term_count<<<(unsigned)blocks, 256, 0, st>>>(col, nnz, cnt);
+    return cudaGetLastError();
+}
+
+__global__ void k_csc_fill(const int64_t *row_ptr, const int32_t *col, const float *val,
+                           int64_t n_docs, const int64_t *col_ptr, int32_t *fill,
+                           int32_t *row_idx, float *cval) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n_docs) return;
+    for (int64_t p = row_ptr[i] + lane; p < row_ptr[i + 1]; p += 32) {
+        const int32_t t = col[p];
+        const int64_t o = col_ptr[t] + atomicAdd(fill + t, 1);
+        row_idx[o] = (int32_t)i;
+        cval[o] = val[p];
+    }
+}
+
+cudaError_t launch_csc_fill(const int64_t *row_ptr, const int32_t *col, const float *val,
+                            int64_t n_docs, const int64_t *col_ptr, int32_t *fill,
+                            int32_t *row_idx, float *cval, cudaStream_t st) {
+    if (n_docs <= 0) return cudaSuccess;
+    const int64_t threads = n_docs * 32;
+    k_csc_fill<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(row_ptr, col, val, n_docs, col_ptr,
+                                                                  fill, row_idx, cval);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// Initial centroids: one warp per centroid writes its document's entries into column j.
+// ------------------------------------------------------------------------------------
+__global__ void k_init_centroids(const int64_t *row_ptr, const int32_t *col, const float *val,
+                                 const int32_t *ids, int32_t k, float *C32, __nv_bfloat16 *C16,
+                                 int64_t ldc) {
+    const int lane = threadIdx.x & 31;
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (j >= k) return;
+    const int64_t i = ids[j];
+    for (int64_t p = row_ptr[i] + lane; p < row_ptr[i + 1]; p += 32) {
+        const int64_t o = (int64_t)col[p] * ldc + j;
+        C32[o] = val[p];
+        if (C16) C16[o] = __float2bfloat16_rn(val[p]);
+    }
+}
+
+cudaError_t launch_init_centroids(const int64_t *row_ptr, const int32_t *col, const float *val,
+                                  const int32_t *ids, int32_t k, float *C32, __nv_bfloat16 *C16,
+                                  int64_t ldc, cudaStream_t st) {
+    const int64_t threads = (int64_t)k * 32;
+    k_init_centroids<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(row_ptr, col, val, ids, k,
+                                                                        C32, C16, ldc);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// Changed clusters (membership reading of Sec. 3.1) and cluster sizes.
+// ------------------------------------------------------------------------------------
+template <bool SMEM_HIST>
+__global__ void k_changed(const int32_t *a_new, const int32_t *a_old, int64_t n_docs, int first,
+                          uint8_t *changed, int32_t *sizes, int32_t k, int32_t *counters) {
+    extern __shared__ int32_t hist[];
+    if (SMEM_HIST) {
+        for (int j = threadIdx.x; j < k; j += blockDim.x) hist[j] = 0;
+        __syncthreads();
+    }
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool moved = false;
+    if (i < n_docs) {
+        const int32_t jn = a_new[i];
+        if (SMEM_HIST) atomicAdd(hist + jn, 1);
+        else atomicAdd(sizes + jn, 1);
+        if (first) {
+            changed[jn] = 1;
+            moved = true;
+        } else {
+            const int32_t jo = a_old[i];
+            if (jo != jn) {
+                changed[jn] = 1;
+                changed[jo] = 1;
+                moved = true;
+            }
+        }
+    }
+    const unsigned m = __ballot_sync(FULL, moved);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(counters + CNT_CHANGED, __popc(m));
+    if (SMEM_HIST) {
+        __syncthreads();
+        for (int j = threadIdx.x; j < k; j += blockDim.x)
+            if (hist[j]) atomicAdd(sizes + j, hist[j]);
+    }
+}
+
+cudaError_t launch_changed(const int32_t *a_new, const int32_t *a_old, int64_t n_docs, int first,
+                           uint8_t *changed, int32_t *sizes, int32_t k, int32_t *counters,
+                           cudaStream_t st) {
+    if (n_docs <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((n_docs + 1023) / 1024);
+    if (k <= 8192)
+        k_changed<true><<<blocks, 1024, (size_t)k * sizeof(int32_t), st>>>(a_new, a_old, n_docs, first,
+                                                                          changed, sizes, k, counters);
+    else
+        k_changed<false><<<blocks, 1024, 0, st>>>(a_new, a_old, n_docs, first, changed, sizes, k,
+                                                  counters);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// Moved list: single block, ascending order by block-wide exclusive scans.
+// ------------------------------------------------------------------------------------
+__global__ void k_compact_moved(const uint8_t *changed, int32_t k, int32_t *moved, int32_t *pos_in_m,
+                                int32_t *counters) {
+    __shared__ int32_t warp_tot[32];
+    __shared__ int32_t base;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int j0 = 0; j0 < k; j0 += blockDim.x) {
+        const int j = j0 + threadIdx.x;
+        const int f = (j < k && changed[j]) ? 1 : 0;
+        const unsigned b = __ballot_sync(FULL, f);
+        const int in_warp = __popc(b & ((1u << lane) - 1u));
+        if (lane == 0) warp_tot[w] = __popc(b);
+        __syncthreads();
+        int before = 0;
+        for (int q = 0; q < w; ++q) before += warp_tot[q];
+        const int idx = base + before + in_warp;
+        if (j < k) {
+            pos_in_m[j] = f ? idx : -1;
+            if (f) moved[idx] = j;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) tot += warp_tot[q];
+            base += tot;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) counters[CNT_MOVED] = base;
+}
+
+cudaError_t launch_compact_moved(const uint8_t *changed, int32_t k, int32_t *moved,
+                                 int32_t *pos_in_m, int32_t *counters, cudaStream_t st) {
+    k_compact_moved<<<1, 1024, 0, st>>>(changed, k, moved, pos_in_m, counters);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// Update passes. Block = THREADS threads, one chunk of consecutive terms (blockIdx.x) and
+// one tile of the moved list (blockIdx.y). Thread tid owns the moved entries
+// m = tid + r * THREADS (r < R) of the tile: it zeroes and reads them, and keeps their
+// FP64 partial sums in registers, so the only cross-thread traffic is the integer
+// shared-memory atomics of the posting walk.
+// ------------------------------------------------------------------------------------
+constexpr int UPD_THREADS = 512;
+constexpr int UPD_R = 8;                        // moved entries per thread per tile
+constexpr int UPD_TILE = UPD_THREADS * UPD_R;   // 4096 entries, 32 KiB of accumulators
+
+template <bool WRITE>
+__global__ void __launch_bounds__(UPD_THREADS) k_update(UpdateArgs u) {
+    extern __shared__ unsigned long long acc[];
+    const int tid = threadIdx.x;
+    const int c = blockIdx.x;
+    const int tile = blockIdx.y;
+    const int m0 = tile * u.m_tile;
+    const int mt = min(u.m_tile, u.n_moved - m0);
+    if (mt <= 0) return;
+    const int64_t *__restrict__ col_ptr = u.col_ptr;
+    const int32_t *__restrict__ row_idx = u.row_idx;
+    const float *__restrict__ cval = u.cval;
+    const int32_t *__restrict__ mdoc = u.mdoc;
+    float *__restrict__ C32 = u.C32;
+    const double inv_scale = 1.0 / u.scale;
+    double p0[UPD_R], p1[UPD_R];
+#pragma unroll
+    for (int r = 0; r < UPD_R; ++r) {
+        p0[r] = 0.0;
+        p1[r] = 0.0;
+    }
+    const int32_t t0 = u.chunk_t0[c], t1 = u.chunk_t1[c];
+    for (int32_t t = t0; t < t1; ++t) {
+#pragma unroll
+        for (int r = 0; r < UPD_R; ++r) {
+            const int m = tid + r * UPD_THREADS;
+            if (m < mt) acc[m] = 0ull;
+        }
+        __syncthreads();
+        const int64_t pb = col_ptr[t], pe = col_ptr[t + 1];
+        for (int64_t p = pb + tid; p < pe; p += UPD_THREADS) {
+            const int mm = __ldg(mdoc + __ldg(row_idx + p)) - m0;
+            if (mm >= 0 && mm < mt) {
+                const long long q = __double2ll_rn((double)__ldg(cval + p) * u.scale);
+                atomicAdd(acc + mm, (unsigned long long)q);
+            }
+        }
+        __syncthreads();
+        const int64_t row = (int64_t)t * u.ldc;
+        if (!WRITE) {
+#pragma unroll
+            for (int r = 0; r < UPD_R; ++r) {
+                const int m = tid + r * UPD_THREADS;
+                if (m >= mt) continue;
+                const long long q = (long long)acc[m];
+                if (q != 0) {
+                    const double S = (double)q * inv_scale;
+                    p0[r] = fma(S, S, p0[r]);
+                }
+            }
+        } else {
+            // phase 1: all loads of the previous centroid values (independent, in flight
+            // together); phase 2: arithmetic and stores
+            float old[UPD_R];
+            int32_t jr[UPD_R];
+            bool live[UPD_R];
+#pragma unroll
+            for (int r = 0; r < UPD_R; ++r) {
+                const int m = tid + r * UPD_THREADS;
+                live[r] = m < mt;
+                jr[r] = live[r] ? __ldg(u.moved + m0 + m) : 0;
+                old[r] = live[r] ? C32[row + jr[r]] : 0.f;
+            }
+#pragma unroll
+            for (int r = 0; r < UPD_R; ++r) {
+                if (!live[r]) continue;
+                const int m = tid + r * UPD_THREADS;
+                const long long q = (long long)acc[m];
+                float cur = old[r];
+                if (__ldg(u.sizes + jr[r]) > 0) {     // an empty cluster keeps its centroid
+                    double cn = 0.0;
+                    if (q != 0) {
+                        const double S = (double)q * inv_scale;
+                        cn = S * __ldg(u.inv_norm + m0 + m);
+                        p0[r] = fma(S, (double)old[r], p0[r]);
+                    }
+                    if (q != 0 || old[r] != 0.f) {
+                        const double dlt = cn - (double)old[r];
+                        p1[r] = fma(dlt, dlt, p1[r]);
+                    }
+                    cur = (float)cn;
+                    C32[row + jr[r]] = cur;
+                    if (u.C16) u.C16[row + jr[r]] = __float2bfloat16_rn(cur);
+                }
+                if (u.precision == 1)
+                    reinterpret_cast<__nv_bfloat16 *>(u.CM)[row + m0 + m] = __float2bfloat16_rn(cur);
+                else
+                    reinterpret_cast<float *>(u.CM)[row + m0 + m] = cur;
+            }
+        }
+        // the next term's zeroing touches only this thread's entries; the barrier after it
+        // orders it before any other thread's atomics
+    }
+    const int64_t ob = ((int64_t)tile * u.n_chunks + c) * u.m_tile;
+#pragma unroll
+    for (int r = 0; r < UPD_R; ++r) {
+        const int m = tid + r * UPD_THREADS;
+        if (m >= mt) continue;
+        if (!WRITE) {
+            u.part_norm[ob + m] = p0[r];
+        } else {
+            u.part_dot[ob + m] = p0[r];
+            u.part_shift[ob + m] = p1[r];
+        }
+    }
+}
+
+// mdoc[i] = position of document i's cluster in the moved list (-1 if not moved).
+__global__ void k_mdoc(const int32_t *a, const int32_t *pos_in_m, int64_t n, int32_t *mdoc) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) mdoc[i] = pos_in_m[a[i]];
+}
+
+cudaError_t launch_mdoc(const int32_t *a, const int32_t *pos_in_m, int64_t n, int32_t *mdoc,
+                        cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_mdoc<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, pos_in_m, n, mdoc);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_update(const UpdateArgs &u, bool write, cudaStream_t st) {
+    if (u.n_chunks <= 0 || u.n_moved <= 0) return cudaSuccess;
+    const int tiles = (u.n_moved + u.m_tile - 1) / u.m_tile;
+    const size_t smem = (size_t)u.m_tile * sizeof(unsigned long long);
+    dim3 grid(u.n_chunks, tiles);
+    cudaError_t e;
+    if (write) {
+        e = cudaFuncSetAttribute(k_update<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_update<true><<<grid, UPD_THREADS, smem, st>>>(u);
+    } else {
+        e = cudaFuncSetAttribute(k_update<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_update<false><<<grid, UPD_THREADS, smem, st>>>(u);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_norm(const UpdateArgs &u, cudaStream_t st) {
+    return launch_update(u, false, st);
+}
+cudaError_t launch_update_write(const UpdateArgs &u, cudaStream_t st) {
+    return launch_update(u, true, st);
+}
+
+int update_tile() { return UPD_TILE; }
+
+// Column sums over chunks, chunk order (deterministic).
+__global__ void k_reduce_parts(const double *part, int32_t n_chunks, int32_t m_tile,
+                               int32_t n_moved, double *out) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n_moved) return;
+    const int tile = m / m_tile, mm = m % m_tile;
+    const double *p = part + (int64_t)tile * n_chunks * m_tile + mm;
+    double s = 0.0;
+    for (int c = 0; c < n_chunks; ++c) s += p[(int64_t)c * m_tile];
+    out[m] = s;
+}
+
+cudaError_t launch_reduce_parts(const double *part, int32_t n_chunks, int32_t m_tile,
+                                int32_t n_moved, double *out, cudaStream_t st) {
+    if (n_moved <= 0) return cudaSuccess;
+    k_reduce_parts<<<(n_moved + 255) / 256, 256, 0, st>>>(part, n_chunks, m_tile, n_moved, out);
+    return cudaGetLastError();
+}
+
+__global__ void k_inv_norm(const double *normsq, int32_t n, double *inv) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < n) inv[m] = normsq[m] > 0.0 ? 1.0 / sqrt(normsq[m]) : 0.0;
+}
+
+cudaError_t launch_inv_norm(const double *normsq, int32_t n_moved, double *inv_norm,
+                            cudaStream_t st) {
+    if (n_moved <= 0) return cudaSuccess;
+    k_inv_norm<<<(n_moved + 255) / 256, 256, 0, st>>>(normsq, n_moved, inv_norm);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// Objective of the step and max squared shift (single block, fixed order):
+//   objective = sum_j S_j . c_j(old) = sum_i x_i . c_{a_i}(old), where for a cluster that
+//   was not recomputed S_j . c_j = ||S_j|| (its centroid is S_j / ||S_j|| from the last
+//   update that recomputed it, and its members are unchanged since), kept in norm_store.
+// ------------------------------------------------------------------------------------
+__global__ void k_finish(const int32_t *pos_in_m, const int32_t *sizes, int32_t k, const double *dot,
+                         const double *normsq, const double *shift, double *norm_store,
+                         double *obj_out, double *shift_out) {
+    __shared__ double so[1024];
+    __shared__ double sm[1024];
+    double o = 0.0, mx = 0.0;
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        const int m = pos_in_m[j];
+        if (sizes[j] <= 0) continue;
+        if (m >= 0) {
+            o += dot[m];
+            if (shift[m] > mx) mx = shift[m];
+            norm_store[j] = sqrt(normsq[m]);
+        } else {
+            o += norm_store[j];
+        }
+    }
+    so[threadIdx.x] = o;
+    sm[threadIdx.x] = mx;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            so[threadIdx.x] += so[threadIdx.x + w];
+            sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + w]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *obj_out = so[0];
+        *shift_out = sm[0];
+    }
+}
+
+cudaError_t launch_finish(const int32_t *pos_in_m, const int32_t *sizes, int32_t k,
+                          const double *dot, const double *normsq, const double *shift,
+                          double *norm_store, double *obj_out, double *shift_out,
+                          cudaStream_t st) {
+    k_finish<<<1, 1024, 0, st>>>(pos_in_m, sizes, k, dot, normsq, shift, norm_store, obj_out,
+                                 shift_out);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// Elementwise helpers.
+// ------------------------------------------------------------------------------------
+__global__ void k_to_bf16(const float *C32, __nv_bfloat16 *C16, int64_t n) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x)
+        C16[q] = __float2bfloat16_rn(C32[q]);
+}
+
+cudaError_t launch_to_bf16(const float *C32, __nv_bfloat16 *C16, int64_t n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t blocks = min((int64_t)152 * 8, (n + 255) / 256);
+    k_to_bf16<<<(unsigned)blocks, 256, 0, st>>>(C32, C16, n);
+    return cudaGetLastError();
+}
+
+__global__ void k_pad_copy(const float *src, int64_t src_ld, float *dst, int64_t dst_ld, int32_t rows,
+                           int32_t cols) {
+    const int64_t n = (int64_t)rows * cols;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = q / cols, c = q % cols;
+        dst[r * dst_ld + c] = src[r * src_ld + c];
+    }
+}
+
+cudaError_t launch_pad_copy(const float *src, int64_t src_ld, float *dst, int64_t dst_ld,
+                            int32_t rows, int32_t cols, cudaStream_t st) {
+    const int64_t n = (int64_t)rows * cols;
+    if (n <= 0) return cudaSuccess;
+    const int64_t blocks = min((int64_t)152 * 8, (n + 255) / 256);
+    k_pad_copy<<<(unsigned)blocks, 256, 0, st>>>(src, src_ld, dst, dst_ld, rows, cols);
+    return cudaGetLastError();
+}
+
+}  // namespace skm

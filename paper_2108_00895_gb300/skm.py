@@ -1,0 +1,348 @@
+"""Python binding of libskm (C ABI in include/skm.h): argument marshalling only.
+
+Every step of the clustering runs in the CUDA library; this module builds the
+argument structs, hands over pointers (numpy arrays for host memory, torch tensors
+for device memory) and turns status codes into exceptions. There is no CPU fallback:
+if the library cannot be built or loaded, every call raises.
+
+The functions ``skm_create``, ``skm_fit``, ``skm_assign``, ``skm_update``,
+``skm_set_centroids``, ``skm_get_centroids``, ``skm_get_stats`` and ``skm_destroy``
+mirror the C entry points of the same names. ``SphericalKMeans`` is a thin owner of
+one context on top of them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+SKM_OK, SKM_ERR_INVALID, SKM_ERR_OOM, SKM_ERR_BUDGET, SKM_ERR_CUDA, SKM_ERR_STATE, SKM_ERR_TIMEOUT = range(7)
+STATUS_NAMES = {0: "SKM_OK", 1: "SKM_ERR_INVALID", 2: "SKM_ERR_OOM", 3: "SKM_ERR_BUDGET",
+                4: "SKM_ERR_CUDA", 5: "SKM_ERR_STATE", 6: "SKM_ERR_TIMEOUT"}
+SKM_FP32, SKM_BF16 = 0, 1
+SKM_PRUNE_NONE, SKM_PRUNE_NCC = 0, 1
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+
+class skm_config(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("precision", ctypes.c_int32), ("prune", ctypes.c_int32),
+                ("max_iter", ctypes.c_int32), ("shift_tol", ctypes.c_double),
+                ("rescore", ctypes.c_int32), ("rescore_tau", ctypes.c_double),
+                ("mem_budget", ctypes.c_size_t), ("device", ctypes.c_int32),
+                ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("alloc_user", ctypes.c_void_p), ("timing", ctypes.c_int32)]
+
+
+class skm_csr(ctypes.Structure):
+    _fields_ = [("n_docs", ctypes.c_int64), ("n_terms", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p),
+                ("values", ctypes.c_void_p), ("on_device", ctypes.c_int32)]
+
+
+class skm_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("sims", ctypes.c_int64), ("fmas", ctypes.c_int64),
+                ("bytes", ctypes.c_int64), ("docs_pruned", ctypes.c_int64),
+                ("docs_full", ctypes.c_int64), ("docs_rescored", ctypes.c_int64),
+                ("docs_rescored_full", ctypes.c_int64), ("moved_total", ctypes.c_int64),
+                ("ms_score", ctypes.c_double), ("ms_decide", ctypes.c_double),
+                ("ms_update", ctypes.c_double), ("launches_score", ctypes.c_int64),
+                ("launches_total", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+EXPORTS = ("skm_config_default", "skm_create", "skm_destroy", "skm_last_error", "skm_fit",
+           "skm_assign", "skm_update", "skm_set_centroids", "skm_get_centroids", "skm_n_terms",
+           "skm_get_stats", "skm_mem_used")
+
+
+def load(build_if_missing: bool = True):
+    """Load libskm.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB_PATH
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libskm.so not found at {path}; run paper_2108_00895_gb300.build")
+        lib = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        st = ctypes.c_int
+        sig = {
+            "skm_config_default": (None, [ctypes.POINTER(skm_config), ctypes.c_int32]),
+            "skm_create": (st, [ctypes.POINTER(skm_config), ctypes.POINTER(P)]),
+            "skm_destroy": (st, [P]),
+            "skm_last_error": (ctypes.c_char_p, [P]),
+            "skm_fit": (st, [P, ctypes.POINTER(skm_csr), P, P, P, P]),
+            "skm_assign": (st, [P, ctypes.POINTER(skm_csr), P, P]),
+            "skm_update": (st, [P, ctypes.POINTER(skm_csr), P, P]),
+            "skm_set_centroids": (st, [P, ctypes.c_int32, P, ctypes.c_int32]),
+            "skm_get_centroids": (st, [P, P, ctypes.c_int32]),
+            "skm_n_terms": (ctypes.c_int32, [P]),
+            "skm_get_stats": (st, [P, ctypes.POINTER(skm_stats)]),
+            "skm_mem_used": (ctypes.c_size_t, [P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+class SkmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(ctx, status: int):
+    if status != SKM_OK:
+        msg = load().skm_last_error(ctx) if ctx else b""
+        raise SkmError(status, (msg or b"").decode(errors="replace"))
+
+
+# ------------------------------------------------------------------ marshalling
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if _is_torch(x):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+def make_csr(docs, n_terms: int | None = None):
+    """skm_csr from a ``synth.Csr`` (host numpy) or a tuple of torch CUDA tensors
+    (row_ptr int64, col_idx int32, values float32) with ``n_terms``. Returns (struct,
+    keep-alive tuple, on_device)."""
+    if isinstance(docs, tuple):
+        rp, ci, va = docs
+        on_dev = int(rp.is_cuda)
+        d = int(n_terms)
+        n = int(rp.shape[0] - 1)
+        e = int(ci.shape[0])
+        keep = (rp, ci, va)
+    else:
+        rp = np.ascontiguousarray(docs.row_ptr, dtype=np.int64)
+        ci = np.ascontiguousarray(docs.col_idx, dtype=np.int32)
+        va = np.ascontiguousarray(docs.values, dtype=np.float32)
+        on_dev = 0
+        d = int(docs.n_terms if n_terms is None else n_terms)
+        n = int(rp.shape[0] - 1)
+        e = int(ci.shape[0])
+        keep = (rp, ci, va)
+    c = skm_csr(n, d, e, _ptr(keep[0]), _ptr(keep[1]), _ptr(keep[2]), on_dev)
+    return c, keep, on_dev
+
+
+# ------------------------------------------------------------------ C entry points
+def skm_config_default(k: int) -> skm_config:
+    cfg = skm_config()
+    load().skm_config_default(ctypes.byref(cfg), int(k))
+    return cfg
+
+
+def skm_create(cfg: skm_config):
+    ctx = ctypes.c_void_p()
+    st = load().skm_create(ctypes.byref(cfg), ctypes.byref(ctx))
+    if st != SKM_OK:
+        raise SkmError(st, "skm_create failed (invalid config, no device, or out of memory)")
+    return ctx
+
+
+def skm_destroy(ctx) -> None:
+    if ctx:
+        load().skm_destroy(ctx)
+
+
+def skm_last_error(ctx) -> str:
+    return (load().skm_last_error(ctx) or b"").decode(errors="replace")
+
+
+def skm_fit(ctx, csr: skm_csr, init_ids, assign_out, objective_out=None, iters_out=None) -> int:
+    it = ctypes.c_int32(0)
+    _check(ctx, load().skm_fit(ctx, ctypes.byref(csr), _ptr(init_ids), _ptr(assign_out),
+                               _ptr(objective_out), ctypes.byref(it)))
+    if iters_out is not None:
+        iters_out[0] = it.value
+    return it.value
+
+
+def skm_assign(ctx, csr: skm_csr, assign_out, score_out=None) -> None:
+    _check(ctx, load().skm_assign(ctx, ctypes.byref(csr), _ptr(assign_out), _ptr(score_out)))
+
+
+def skm_update(ctx, csr: skm_csr, assign) -> int:
+    n = ctypes.c_int32(0)
+    _check(ctx, load().skm_update(ctx, ctypes.byref(csr), _ptr(assign), ctypes.byref(n)))
+    return n.value
+
+
+def skm_set_centroids(ctx, n_terms: int, centroids, on_device: int) -> None:
+    _check(ctx, load().skm_set_centroids(ctx, int(n_terms), _ptr(centroids), int(on_device)))
+
+
+def skm_get_centroids(ctx, out, on_device: int) -> None:
+    _check(ctx, load().skm_get_centroids(ctx, _ptr(out), int(on_device)))
+
+
+def skm_get_stats(ctx) -> skm_stats:
+    s = skm_stats()
+    _check(ctx, load().skm_get_stats(ctx, ctypes.byref(s)))
+    return s
+
+
+# ------------------------------------------------------------------ owner class
+class _TorchAllocator:
+    """Device memory from PyTorch's caching allocator, handed to the library."""
+
+    def __init__(self, device: int, stream_ptr: int):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.stream = stream_ptr
+        self.alloc_cb = ALLOC_FN(self._alloc)
+        self.free_cb = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, user):
+        try:
+            return self.torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream or None)
+        except Exception:      # out of memory: the library reports SKM_ERR_OOM
+            return None
+
+    def _free(self, ptr, nbytes, user):
+        self.torch.cuda.caching_allocator_delete(int(ptr))
+
+
+@dataclass
+class FitResult:
+    assign: np.ndarray
+    objective: np.ndarray
+    iters: int
+    stats: dict
+
+
+class SphericalKMeans:
+    """One libskm context: exact spherical k-means on one GPU.
+
+    precision: "fp32" or "bf16" (scored centroid copy); prune: "none" or "ncc"
+    (Sec. 3.1 skip); rescore: FP64 rescoring of near ties; tau: margin threshold.
+    """
+
+    def __init__(self, k: int, precision: str = "fp32", prune: str = "none", max_iter: int = 20,
+                 shift_tol: float = -1.0, rescore: bool = True, tau: float = 0.0, device: int = 0,
+                 stream: int | None = None, mem_budget: int = 0, timing: bool = False,
+                 allocator: str = "torch"):
+        self.lib = load()
+        cfg = skm_config_default(k)
+        cfg.precision = {"fp32": SKM_FP32, "bf16": SKM_BF16}[precision]
+        cfg.prune = {"none": SKM_PRUNE_NONE, "ncc": SKM_PRUNE_NCC}[prune]
+        cfg.max_iter = int(max_iter)
+        cfg.shift_tol = float(shift_tol)
+        cfg.rescore = int(bool(rescore))
+        cfg.rescore_tau = float(tau)
+        cfg.mem_budget = int(mem_budget)
+        cfg.device = int(device)
+        cfg.timing = int(bool(timing))
+        if stream is None and allocator == "torch":
+            import torch
+            stream = torch.cuda.current_stream(device).cuda_stream
+        cfg.stream = stream or None
+        self._alloc = None
+        if allocator == "torch":
+            self._alloc = _TorchAllocator(int(device), int(stream or 0))
+            cfg.alloc = self._alloc.alloc_cb
+            cfg.free = self._alloc.free_cb
+        self.cfg = cfg
+        self.k = int(k)
+        self.max_iter = int(max_iter)
+        self.ctx = skm_create(cfg)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            skm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # --------------------------------------------------------------- calls
+    def fit(self, docs, init_ids, n_terms: int | None = None, assign_out=None) -> FitResult:
+        csr, keep, on_dev = make_csr(docs, n_terms)
+        ids = np.ascontiguousarray(init_ids, dtype=np.int32)
+        if assign_out is None:
+            if on_dev:
+                import torch
+                assign_out = torch.empty(csr.n_docs, dtype=torch.int32, device=keep[0].device)
+            else:
+                assign_out = np.empty(csr.n_docs, np.int32)
+        obj = np.zeros(self.max_iter, np.float64)
+        it = skm_fit(self.ctx, csr, ids, assign_out, obj)
+        return FitResult(assign_out, obj[:it].copy(), it, skm_get_stats(self.ctx).as_dict())
+
+    def assign(self, docs, n_terms: int | None = None, assign_out=None, score_out=None,
+               want_scores: bool = True):
+        csr, keep, on_dev = make_csr(docs, n_terms)
+        if assign_out is None:
+            if on_dev:
+                import torch
+                assign_out = torch.empty(csr.n_docs, dtype=torch.int32, device=keep[0].device)
+                if want_scores and score_out is None:
+                    score_out = torch.empty(csr.n_docs, dtype=torch.float32, device=keep[0].device)
+            else:
+                assign_out = np.empty(csr.n_docs, np.int32)
+                if want_scores and score_out is None:
+                    score_out = np.empty(csr.n_docs, np.float32)
+        skm_assign(self.ctx, csr, assign_out, score_out)
+        return assign_out, score_out
+
+    def update(self, docs, assign, n_terms: int | None = None) -> int:
+        csr, keep, on_dev = make_csr(docs, n_terms)
+        a = assign if on_dev else np.ascontiguousarray(assign, dtype=np.int32)
+        return skm_update(self.ctx, csr, a)
+
+    def set_centroids(self, C) -> None:
+        if _is_torch(C):
+            C = C.contiguous()
+            skm_set_centroids(self.ctx, C.shape[0], C, int(C.is_cuda))
+        else:
+            C = np.ascontiguousarray(C, dtype=np.float32)
+            skm_set_centroids(self.ctx, C.shape[0], C, 0)
+
+    def centroids(self) -> np.ndarray:
+        d = self.lib.skm_n_terms(self.ctx)
+        out = np.empty((d, self.k), np.float32)
+        skm_get_centroids(self.ctx, out, 0)
+        return out
+
+    def stats(self) -> dict:
+        return skm_get_stats(self.ctx).as_dict()
+
+    def mem_used(self) -> int:
+        return int(self.lib.skm_mem_used(self.ctx))

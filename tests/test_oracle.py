@@ -273,3 +273,12 @@ def test_objective_matches_sum_of_best():
     r = oracle.fit(docs, k, ids, 4)
     a, s1, _ = oracle.assign(docs, r.C)
     assert abs(oracle.objective(docs, r.C, a) - s1.sum()) < 1e-12
+
+
+def test_centroids_subset_matches_full_update():
+    docs, ids, k = _tiny(141)
+    rng = np.random.default_rng(141)
+    a = rng.integers(0, k, docs.n_docs).astype(np.int32)
+    full = oracle.update(docs, a, np.zeros((docs.n_terms, k))).C
+    sel = np.array([3, 0, 7])
+    np.testing.assert_array_equal(oracle.centroids_subset(docs, a, sel), full[:, sel])
