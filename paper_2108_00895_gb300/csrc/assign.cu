@@ -5,10 +5,32 @@
 // one FP32 fused multiply-add per nonzero per centroid. The chain for a given (i, j) is the
 // same whichever launch computes it (full matrix or compacted moved-centroid matrix), so a
 // score is a pure function of (x_i, c_j): the pruned and the full pass agree bit for bit.
+#include <cstdlib>
+
 #include "skm_internal.cuh"
 #include "skm_kernels.cuh"
 
 namespace skm {
+
+// acc[q] += v * (two consecutive columns of the loaded row segment), one paired FP32
+// fused multiply-add per two columns; each half rounds exactly like a scalar fmaf.
+template <typename CT, int NV>
+__device__ __forceinline__ void fma_row(float2 (&acc)[NV * 16 / (int)sizeof(CT) / 2], float v,
+                                        const uint4 (&w)[NV]) {
+    const float2 vv = make_float2(v, v);
+#pragma unroll
+    for (int u = 0; u < NV; ++u) {
+        const uint32_t ww[4] = {w[u].x, w[u].y, w[u].z, w[u].w};
+        if constexpr (sizeof(CT) == 4) {
+            acc[u * 2 + 0] = __ffma2_rn(vv, make_float2(__uint_as_float(ww[0]), __uint_as_float(ww[1])), acc[u * 2 + 0]);
+            acc[u * 2 + 1] = __ffma2_rn(vv, make_float2(__uint_as_float(ww[2]), __uint_as_float(ww[3])), acc[u * 2 + 1]);
+        } else {
+#pragma unroll
+            for (int h = 0; h < 4; ++h)
+                acc[u * 4 + h] = __ffma2_rn(vv, make_float2(bf16lo(ww[h]), bf16hi(ww[h])), acc[u * 4 + h]);
+        }
+    }
+}
 
 // ------------------------------------------------------------------------------------
 // k_score: one warp per (document, slice). Lane l owns, for u in [0, NV), the EPV columns
@@ -18,11 +40,14 @@ namespace skm {
 // ------------------------------------------------------------------------------------
 template <typename CT, int NV>
 __global__ void __launch_bounds__(256) k_score(ScoreArgs a) {
-    constexpr int EPV = 16 / (int)sizeof(CT);
-    constexpr int J = NV * EPV;
-    constexpr int KS = 32 * J;
+    constexpr int EPV = 16 / (int)sizeof(CT);   // elements per 16-byte vector
+    constexpr int J = NV * EPV;                  // columns per lane
+    constexpr int KS = 32 * J;                   // columns per slice
+    constexpr int G = NV >= 4 ? 2 : 4;           // nonzeros whose rows are loaded together
+    __shared__ int2 stage[8][32];                // per warp: 32 (t, x) pairs
     const int lane = threadIdx.x & 31;
-    const int pos = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int wib = threadIdx.x >> 5;
+    const int pos = blockIdx.x * 8 + wib;
     if (pos >= a.n_list) return;
     const int slice = blockIdx.y;
     const int64_t i = a.doc_list ? (int64_t)a.doc_list[pos] : (int64_t)pos;
@@ -30,43 +55,37 @@ __global__ void __launch_bounds__(256) k_score(ScoreArgs a) {
     const int64_t j0 = (int64_t)slice * KS;
     const CT *Cs = reinterpret_cast<const CT *>(a.C) + j0 + lane * EPV;
 
-    float acc[J];
+    float2 acc[J / 2];
 #pragma unroll
-    for (int q = 0; q < J; ++q) acc[q] = 0.f;
+    for (int q = 0; q < J / 2; ++q) acc[q] = make_float2(0.f, 0.f);
 
     for (int64_t b = beg; b < end; b += 32) {
         const int n = (int)min((int64_t)32, end - b);
-        int mt = 0;
-        float mv = 0.f;
-        if (lane < n) {
-            mt = __ldg(a.col + b + lane);
-            mv = __ldg(a.val + b + lane);
+        __syncwarp();
+        if (lane < n) stage[wib][lane] = make_int2(__ldg(a.col + b + lane), __float_as_int(__ldg(a.val + b + lane)));
+        __syncwarp();
+        int q = 0;
+        for (; q + G <= n; q += G) {
+            uint4 w[G][NV];
+            float v[G];
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const int2 tv = stage[wib][q + g];
+                v[g] = __int_as_float(tv.y);
+                const CT *row = Cs + (int64_t)tv.x * a.ldc;
+#pragma unroll
+                for (int u = 0; u < NV; ++u) w[g][u] = ldg16(row + u * 32 * EPV);
+            }
+#pragma unroll
+            for (int g = 0; g < G; ++g) fma_row<CT, NV>(acc, v[g], w[g]);
         }
-        for (int q = 0; q < n; ++q) {
-            const int t = __shfl_sync(FULL, mt, q);
-            const float v = __shfl_sync(FULL, mv, q);
-            const CT *row = Cs + (int64_t)t * a.ldc;
+        for (; q < n; ++q) {
+            const int2 tv = stage[wib][q];
+            const CT *row = Cs + (int64_t)tv.x * a.ldc;
             uint4 w[NV];
 #pragma unroll
             for (int u = 0; u < NV; ++u) w[u] = ldg16(row + u * 32 * EPV);
-#pragma unroll
-            for (int u = 0; u < NV; ++u) {
-                if constexpr (sizeof(CT) == 4) {
-                    acc[u * 4 + 0] = __fmaf_rn(v, __uint_as_float(w[u].x), acc[u * 4 + 0]);
-                    acc[u * 4 + 1] = __fmaf_rn(v, __uint_as_float(w[u].y), acc[u * 4 + 1]);
-                    acc[u * 4 + 2] = __fmaf_rn(v, __uint_as_float(w[u].z), acc[u * 4 + 2]);
-                    acc[u * 4 + 3] = __fmaf_rn(v, __uint_as_float(w[u].w), acc[u * 4 + 3]);
-                } else {
-                    acc[u * 8 + 0] = __fmaf_rn(v, bf16lo(w[u].x), acc[u * 8 + 0]);
-                    acc[u * 8 + 1] = __fmaf_rn(v, bf16hi(w[u].x), acc[u * 8 + 1]);
-                    acc[u * 8 + 2] = __fmaf_rn(v, bf16lo(w[u].y), acc[u * 8 + 2]);
-                    acc[u * 8 + 3] = __fmaf_rn(v, bf16hi(w[u].y), acc[u * 8 + 3]);
-                    acc[u * 8 + 4] = __fmaf_rn(v, bf16lo(w[u].z), acc[u * 8 + 4]);
-                    acc[u * 8 + 5] = __fmaf_rn(v, bf16hi(w[u].z), acc[u * 8 + 5]);
-                    acc[u * 8 + 6] = __fmaf_rn(v, bf16lo(w[u].w), acc[u * 8 + 6]);
-                    acc[u * 8 + 7] = __fmaf_rn(v, bf16hi(w[u].w), acc[u * 8 + 7]);
-                }
-            }
+            fma_row<CT, NV>(acc, __int_as_float(tv.y), w);
         }
     }
 
@@ -81,7 +100,8 @@ __global__ void __launch_bounds__(256) k_score(ScoreArgs a) {
             const int64_t c = j0 + u * 32 * EPV + lane * EPV + e;
             if (c < a.ncols) {
                 const int id = a.col_ids ? __ldg(a.col_ids + c) : (int)c;
-                topt_insert(ls, lj, acc[u * EPV + e], id);
+                const int qq = (u * EPV + e) >> 1;
+                topt_insert(ls, lj, (e & 1) ? acc[qq].y : acc[qq].x, id);
             }
         }
     }
@@ -98,8 +118,14 @@ __global__ void __launch_bounds__(256) k_score(ScoreArgs a) {
 }
 
 int slice_width(int precision, int k) {
-    // FP32: NV = 2 (8 columns per lane, 256 per slice); BF16: NV = 2 (16 per lane, 512).
-    // Small k uses the narrowest shape so that padded columns stay few.
+    // Columns per scoring slice: 32 lanes x NV 16-byte vectors. FP32: 128/256/512 for NV
+    // 1/2/4; BF16: 256/512/1024. Small k uses the narrowest shape so that padded columns
+    // stay few; SKM_SLICE overrides the choice (tuning).
+    if (const char *env = getenv("SKM_SLICE")) {
+        const int v = atoi(env);
+        if (precision == 0 && (v == 128 || v == 256 || v == 512)) return v;
+        if (precision == 1 && (v == 256 || v == 512 || v == 1024)) return v;
+    }
     if (precision == 0) return k <= 128 ? 128 : 256;
     return k <= 256 ? 256 : 512;
 }
@@ -110,11 +136,19 @@ cudaError_t launch_score(const ScoreArgs &a, int precision, int slice_cols, cuda
     if (n_slices <= 0) return cudaSuccess;
     dim3 grid((a.n_list + 7) / 8, n_slices);
     if (precision == 0) {
-        if (slice_cols == 128) k_score<float, 1><<<grid, 256, 0, st>>>(a);
-        else k_score<float, 2><<<grid, 256, 0, st>>>(a);
+        switch (slice_cols) {
+            case 128: k_score<float, 1><<<grid, 256, 0, st>>>(a); break;
+            case 256: k_score<float, 2><<<grid, 256, 0, st>>>(a); break;
+            case 512: k_score<float, 4><<<grid, 256, 0, st>>>(a); break;
+            default: return cudaErrorInvalidValue;
+        }
     } else {
-        if (slice_cols == 256) k_score<__nv_bfloat16, 1><<<grid, 256, 0, st>>>(a);
-        else k_score<__nv_bfloat16, 2><<<grid, 256, 0, st>>>(a);
+        switch (slice_cols) {
+            case 256: k_score<__nv_bfloat16, 1><<<grid, 256, 0, st>>>(a); break;
+            case 512: k_score<__nv_bfloat16, 2><<<grid, 256, 0, st>>>(a); break;
+            case 1024: k_score<__nv_bfloat16, 4><<<grid, 256, 0, st>>>(a); break;
+            default: return cudaErrorInvalidValue;
+        }
     }
     return cudaGetLastError();
 }
@@ -354,9 +388,10 @@ cudaError_t launch_full64(const Full64Args &a, int n_max, cudaStream_t st) {
 // unchanged. Warp-aggregated appends; list order does not affect any result.
 // ------------------------------------------------------------------------------------
 __global__ void k_partition(PartitionArgs a) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    bool pr = false, in = i < a.n_docs;
+    bool pr = false, in = pos < a.n_docs;
+    const int64_t i = in ? (int64_t)a.order[pos] : 0;
     if (in) pr = a.prune && a.clean[i] && !a.changed[a.a_old[i]];
     const unsigned mp = __ballot_sync(FULL, in && pr);
     const unsigned mf = __ballot_sync(FULL, in && !pr);

@@ -49,19 +49,19 @@ struct skm_ctx {
     int32_t d = 0;
     int64_t ldc = 0;
     int slice = 0;
-    Buf C32, C16, CM, norm_store;
+    Buf C32, C16, CM, norm_store, sq_store;
 
     // staged documents (host inputs are copied here)
     Buf d_row_ptr, d_col, d_val;
     // transposed postings
     Buf col_ptr, row_idx, cval, tcount, chunk_t0, chunk_t1;
     // per-document state
-    Buf abuf[2], s_state, r_state, clean, mdoc;
+    Buf abuf[2], s_state, r_state, clean, mdoc, order, order_hist;
     Buf part_s, part_j;
     Buf list_a, list_b, rs_doc, rs_cand, refull, full64;
     // per-cluster state
-    Buf changed, sizes, moved, pos_in_m, normsq, inv_norm, dot, shift;
-    Buf part_norm, part_dot, part_shift;
+    Buf changed, sizes, moved, pos_in_m, normsq, inv_norm, dot_fx, newsq;
+    Buf part_norm, part_sq;
     Buf counters, counters64, scal, obj, init_ids;
     int32_t *h_counters = nullptr;  // pinned mirror
     unsigned long long *h_counters64 = nullptr;
@@ -276,11 +276,13 @@ skm_status ensure_centroids(skm_ctx *ctx, int32_t d, bool zero) {
     if (ctx->cfg.precision == SKM_BF16) SKM_TRY(ensure(ctx, ctx->C16, n * sizeof(__nv_bfloat16)));
     SKM_TRY(ensure(ctx, ctx->CM, n * (ctx->cfg.precision == SKM_BF16 ? 2 : 4)));
     SKM_TRY(ensure(ctx, ctx->norm_store, sizeof(double) * k));
+    SKM_TRY(ensure(ctx, ctx->sq_store, sizeof(double) * k));
     if (fresh || zero) {
         SKM_CUDA(cudaMemsetAsync(ctx->C32.p, 0, n * sizeof(float), ctx->st));
         if (ctx->C16.p) SKM_CUDA(cudaMemsetAsync(ctx->C16.p, 0, n * sizeof(__nv_bfloat16), ctx->st));
         SKM_CUDA(cudaMemsetAsync(ctx->CM.p, 0, n * (ctx->cfg.precision == SKM_BF16 ? 2 : 4), ctx->st));
         SKM_CUDA(cudaMemsetAsync(ctx->norm_store.p, 0, sizeof(double) * k, ctx->st));
+        SKM_CUDA(cudaMemsetAsync(ctx->sq_store.p, 0, sizeof(double) * k, ctx->st));
     }
     ctx->d = d;
     return SKM_OK;
@@ -295,8 +297,8 @@ skm_status ensure_cluster_bufs(skm_ctx *ctx) {
     SKM_TRY(ensure(ctx, ctx->pos_in_m, sizeof(int32_t) * k));
     SKM_TRY(ensure(ctx, ctx->normsq, sizeof(double) * k));
     SKM_TRY(ensure(ctx, ctx->inv_norm, sizeof(double) * k));
-    SKM_TRY(ensure(ctx, ctx->dot, sizeof(double) * k));
-    SKM_TRY(ensure(ctx, ctx->shift, sizeof(double) * k));
+    SKM_TRY(ensure(ctx, ctx->dot_fx, sizeof(unsigned long long) * k));
+    SKM_TRY(ensure(ctx, ctx->newsq, sizeof(double) * k));
     return SKM_OK;
 }
 
@@ -310,6 +312,8 @@ skm_status ensure_doc_bufs(skm_ctx *ctx, int64_t n) {
     SKM_TRY(ensure(ctx, ctx->r_state, sizeof(float) * n));
     SKM_TRY(ensure(ctx, ctx->clean, n));
     SKM_TRY(ensure(ctx, ctx->mdoc, sizeof(int32_t) * n));
+    SKM_TRY(ensure(ctx, ctx->order, sizeof(int32_t) * n));
+    SKM_TRY(ensure(ctx, ctx->order_hist, sizeof(int32_t) * 4096));
     SKM_TRY(ensure(ctx, ctx->part_s, sizeof(float) * n * n_slices * TOPT));
     SKM_TRY(ensure(ctx, ctx->part_j, sizeof(int32_t) * n * n_slices * TOPT));
     SKM_TRY(ensure(ctx, ctx->list_a, sizeof(int32_t) * n));
@@ -385,8 +389,7 @@ skm_status build_postings(skm_ctx *ctx, const DevCsr &dc, Postings &pg) {
     const int64_t tiles = (k + tile - 1) / tile;
     const size_t parts = (size_t)tiles * pg.n_chunks * tile;
     SKM_TRY(ensure(ctx, ctx->part_norm, sizeof(double) * parts));
-    SKM_TRY(ensure(ctx, ctx->part_dot, sizeof(double) * parts));
-    SKM_TRY(ensure(ctx, ctx->part_shift, sizeof(double) * parts));
+    SKM_TRY(ensure(ctx, ctx->part_sq, sizeof(double) * parts));
     // the transient host vectors must outlive the async copies
     SKM_TRY(sync(ctx));
     return SKM_OK;
@@ -502,8 +505,9 @@ skm_status rescore_queues(skm_ctx *ctx, const DevCsr &dc, int32_t *a_new, float 
 
 // One update step: changed flags, moved list, the two posting passes, objective and shift.
 // Returns the number of documents whose assignment changed and |M| through the counters.
-skm_status update_step(skm_ctx *ctx, const Postings &pg, const int32_t *a_new, const int32_t *a_old,
-                       int64_t n_docs, bool first, bool converged_check, bool *converged, int iter) {
+skm_status update_step(skm_ctx *ctx, const DevCsr &dc, const Postings &pg, const int32_t *a_new,
+                       const int32_t *a_old, int64_t n_docs, bool first, bool converged_check,
+                       bool *converged, int iter) {
     const int32_t k = ctx->cfg.k;
     Timed tm(ctx, ctx->ev_update);
     SKM_CUDA(cudaMemsetAsync(ctx->changed.p, 0, k, ctx->st));
@@ -519,7 +523,16 @@ skm_status update_step(skm_ctx *ctx, const Postings &pg, const int32_t *a_new, c
     *converged = converged_check && !first && n_changed_docs == 0;
     double *obj = P<double>(ctx->obj) + iter;
     double *shf = P<double>(ctx->scal);
+    // fixed-point scale of the per-document objective terms (each in [0, 1 + 1e-5])
+    int nb = 0;
+    while ((int64_t(1) << nb) < n_docs + 1) ++nb;
+    const double dot_scale = std::ldexp(1.0, 61 - nb);
     if (!*converged && n_moved > 0) {
+        SKM_CUDA(launch_mdoc(a_new, P<int32_t>(ctx->pos_in_m), n_docs, P<int32_t>(ctx->mdoc), ctx->st));
+        SKM_CUDA(cudaMemsetAsync(ctx->dot_fx.p, 0, sizeof(unsigned long long) * n_moved, ctx->st));
+        SKM_CUDA(launch_doc_obj(dc.row_ptr, dc.col, dc.val, n_docs, a_new, P<int32_t>(ctx->mdoc),
+                                P<float>(ctx->C32), ctx->ldc, dot_scale,
+                                P<unsigned long long>(ctx->dot_fx), ctx->st));
         UpdateArgs u{};
         u.n_chunks = pg.n_chunks;
         u.chunk_t0 = P<int32_t>(ctx->chunk_t0);
@@ -544,23 +557,21 @@ skm_status update_step(skm_ctx *ctx, const Postings &pg, const int32_t *a_new, c
         u.CM = ctx->CM.p;
         u.precision = ctx->cfg.precision;
         u.ldc = ctx->ldc;
-        u.part_dot = P<double>(ctx->part_dot);
-        u.part_shift = P<double>(ctx->part_shift);
-        SKM_CUDA(launch_mdoc(a_new, P<int32_t>(ctx->pos_in_m), n_docs, P<int32_t>(ctx->mdoc), ctx->st));
+        u.part_sq = P<double>(ctx->part_sq);
         SKM_CUDA(launch_update_norm(u, ctx->st));
         SKM_CUDA(launch_reduce_parts(u.part_norm, pg.n_chunks, u.m_tile, n_moved, P<double>(ctx->normsq), ctx->st));
         SKM_CUDA(launch_inv_norm(P<double>(ctx->normsq), n_moved, P<double>(ctx->inv_norm), ctx->st));
+        SKM_CUDA(launch_zero_moved(u.moved, u.sizes, n_moved, ctx->d, u.C32, u.C16, u.CM, u.precision, u.ldc,
+                                   ctx->st));
         SKM_CUDA(launch_update_write(u, ctx->st));
-        SKM_CUDA(launch_reduce_parts(u.part_dot, pg.n_chunks, u.m_tile, n_moved, P<double>(ctx->dot), ctx->st));
-        SKM_CUDA(launch_reduce_parts(u.part_shift, pg.n_chunks, u.m_tile, n_moved, P<double>(ctx->shift), ctx->st));
-        ctx->stats.launches_total += 7;
+        SKM_CUDA(launch_reduce_parts(u.part_sq, pg.n_chunks, u.m_tile, n_moved, P<double>(ctx->newsq), ctx->st));
+        ctx->stats.launches_total += 8;
     }
-    if (*converged) {
-        // no moved cluster: pos_in_m is -1 everywhere and the objective is sum_j ||S_j||
-    }
-    SKM_CUDA(launch_finish(P<int32_t>(ctx->pos_in_m), P<int32_t>(ctx->sizes), k, P<double>(ctx->dot),
-                           P<double>(ctx->normsq), P<double>(ctx->shift), P<double>(ctx->norm_store),
-                           obj, shf, ctx->st));
+    // with no moved cluster pos_in_m is -1 everywhere and the objective is sum_j ||S_j||
+    SKM_CUDA(launch_finish(P<int32_t>(ctx->pos_in_m), P<int32_t>(ctx->sizes), k,
+                           P<unsigned long long>(ctx->dot_fx), 1.0 / dot_scale, P<double>(ctx->normsq),
+                           P<double>(ctx->newsq), P<double>(ctx->norm_store), P<double>(ctx->sq_store), obj,
+                           shf, ctx->st));
     ctx->stats.launches_total++;
     return SKM_OK;
 }
@@ -627,10 +638,10 @@ skm_status skm_destroy(skm_ctx *ctx) {
     Buf *all[] = {&ctx->C32, &ctx->C16, &ctx->CM, &ctx->norm_store, &ctx->d_row_ptr, &ctx->d_col,
                   &ctx->d_val, &ctx->col_ptr, &ctx->row_idx, &ctx->cval, &ctx->tcount, &ctx->chunk_t0,
                   &ctx->chunk_t1, &ctx->abuf[0], &ctx->abuf[1], &ctx->s_state, &ctx->r_state,
-                  &ctx->clean, &ctx->mdoc, &ctx->part_s, &ctx->part_j, &ctx->list_a, &ctx->list_b, &ctx->rs_doc,
+                  &ctx->clean, &ctx->mdoc, &ctx->order, &ctx->order_hist, &ctx->part_s, &ctx->part_j, &ctx->list_a, &ctx->list_b, &ctx->rs_doc,
                   &ctx->rs_cand, &ctx->refull, &ctx->full64, &ctx->changed, &ctx->sizes, &ctx->moved,
-                  &ctx->pos_in_m, &ctx->normsq, &ctx->inv_norm, &ctx->dot, &ctx->shift,
-                  &ctx->part_norm, &ctx->part_dot, &ctx->part_shift, &ctx->counters, &ctx->counters64, &ctx->scal,
+                  &ctx->pos_in_m, &ctx->normsq, &ctx->inv_norm, &ctx->dot_fx, &ctx->newsq,
+                  &ctx->part_norm, &ctx->part_sq, &ctx->sq_store, &ctx->counters, &ctx->counters64, &ctx->scal,
                   &ctx->obj, &ctx->init_ids};
     for (Buf *b : all) release(ctx, *b);
     if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
@@ -687,10 +698,12 @@ skm_status skm_fit(skm_ctx *ctx, const skm_csr *docs, const int32_t *init_doc_id
     SKM_CUDA(cudaMemcpyAsync(ctx->init_ids.p, init_doc_ids, sizeof(int32_t) * k, cudaMemcpyHostToDevice, ctx->st));
     SKM_CUDA(launch_init_centroids(dc.row_ptr, dc.col, dc.val, P<int32_t>(ctx->init_ids), k, P<float>(ctx->C32),
                                    ctx->cfg.precision == SKM_BF16 ? P<__nv_bfloat16>(ctx->C16) : nullptr,
-                                   ctx->ldc, ctx->st));
+                                   ctx->ldc, P<double>(ctx->sq_store), ctx->st));
     ctx->stats.launches_total++;
     SKM_CUDA(cudaMemsetAsync(ctx->clean.p, 0, N, ctx->st));
     SKM_CUDA(cudaMemsetAsync(ctx->changed.p, 1, k, ctx->st));
+    SKM_CUDA(launch_order_by_length(dc.row_ptr, N, P<int32_t>(ctx->order_hist), P<int32_t>(ctx->order), ctx->st));
+    ctx->stats.launches_total += 3;
 
     const bool prune = ctx->cfg.prune == SKM_PRUNE_NCC;
     int32_t n_moved_prev = k;
@@ -703,10 +716,11 @@ skm_status skm_fit(skm_ctx *ctx, const skm_csr *docs, const int32_t *init_doc_id
         int32_t *a_new = P<int32_t>(ctx->abuf[cur]);
         SKM_TRY(reset_counters(ctx));
         int32_t n_pruned = 0, n_full = (int32_t)N;
-        const int32_t *full_list = nullptr;
+        const int32_t *full_list = P<int32_t>(ctx->order);
         if (prune && !first) {
             PartitionArgs pa{};
             pa.n_docs = N;
+            pa.order = P<int32_t>(ctx->order);
             pa.prune = 1;
             pa.clean = P<uint8_t>(ctx->clean);
             pa.changed = P<uint8_t>(ctx->changed);
@@ -750,7 +764,7 @@ skm_status skm_fit(skm_ctx *ctx, const skm_csr *docs, const int32_t *init_doc_id
         ctx->stats.bytes += 8 * (dc.nnz + nnz_refull) + 20 * (N + n_refull) + pg.d_eff * cols_needed * elt;
         SKM_TRY(rescore_queues(ctx, dc, a_new, nullptr));
         bool converged = false;
-        SKM_TRY(update_step(ctx, pg, a_new, a_old, N, first, true, &converged, t - 1));
+        SKM_TRY(update_step(ctx, dc, pg, a_new, a_old, N, first, true, &converged, t - 1));
         n_moved_prev = ctx->h_counters[CNT_MOVED];
         cur ^= 1;
         if (converged) break;
@@ -797,7 +811,10 @@ skm_status skm_assign(skm_ctx *ctx, const skm_csr *docs, int32_t *assign_out, fl
     } else {
         score_dev = score_out;
     }
-    skm_status s = score_and_decide(ctx, dc, nullptr, (int32_t)N, false, ctx->cfg.k, nullptr, a_new, score_dev);
+    SKM_CUDA(launch_order_by_length(dc.row_ptr, N, P<int32_t>(ctx->order_hist), P<int32_t>(ctx->order), ctx->st));
+    ctx->stats.launches_total += 3;
+    skm_status s = score_and_decide(ctx, dc, P<int32_t>(ctx->order), (int32_t)N, false, ctx->cfg.k, nullptr, a_new,
+                                    score_dev);
     if (s == SKM_OK) s = rescore_queues(ctx, dc, a_new, score_dev);
     if (s == SKM_OK) {
         const cudaMemcpyKind kind = docs->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -850,7 +867,7 @@ skm_status skm_update(skm_ctx *ctx, const skm_csr *docs, const int32_t *assign, 
     SKM_TRY(build_postings(ctx, dc, pg));
     SKM_TRY(reset_counters(ctx));
     bool conv = false;
-    SKM_TRY(update_step(ctx, pg, a_dev, nullptr, N, true, false, &conv, 0));
+    SKM_TRY(update_step(ctx, dc, pg, a_dev, nullptr, N, true, false, &conv, 0));
     SKM_TRY(sync(ctx));
     collect_times(ctx);
     if (n_changed_out) *n_changed_out = ctx->h_counters[CNT_MOVED];
@@ -870,6 +887,7 @@ skm_status skm_set_centroids(skm_ctx *ctx, int32_t n_terms, const float *centroi
         SKM_CUDA(launch_to_bf16(P<float>(ctx->C32), P<__nv_bfloat16>(ctx->C16), (int64_t)n_terms * ctx->ldc, ctx->st));
         ctx->stats.launches_total++;
     }
+    SKM_CUDA(launch_col_sq(P<float>(ctx->C32), ctx->ldc, n_terms, k, P<double>(ctx->sq_store), ctx->st));
     return sync(ctx);
 }
 

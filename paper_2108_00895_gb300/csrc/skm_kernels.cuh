@@ -74,6 +74,7 @@ struct Full64Args {
 
 struct PartitionArgs {
     int64_t n_docs;
+    const int32_t *order;      // documents are visited in this order
     int prune;
     const uint8_t *clean;
     const uint8_t *changed;
@@ -97,16 +98,21 @@ cudaError_t launch_partition(const PartitionArgs &a, cudaStream_t st);
 cudaError_t launch_validate(const int64_t *row_ptr, const int32_t *col, const float *val,
                             int64_t n_docs, int32_t n_terms, int32_t *err, cudaStream_t st);
 
+// order[] = document ids by decreasing number of nonzeros; hist is scratch of 4096 ints.
+cudaError_t launch_order_by_length(const int64_t *row_ptr, int64_t n, int32_t *hist, int32_t *order,
+                                   cudaStream_t st);
+
 // Term-major transpose (CSC) of the collection: counts per term, then a fill.
 cudaError_t launch_term_count(const int32_t *col, int64_t nnz, int32_t *cnt, cudaStream_t st);
 cudaError_t launch_csc_fill(const int64_t *row_ptr, const int32_t *col, const float *val,
                             int64_t n_docs, const int64_t *col_ptr, int32_t *fill,
                             int32_t *row_idx, float *cval, cudaStream_t st);
 
-// Initial centroids c_j = x_{ids[j]} (the matrices must be zero beforehand).
+// Initial centroids c_j = x_{ids[j]} (the matrices must be zero beforehand); sq[j] gets
+// the squared norm of the stored column.
 cudaError_t launch_init_centroids(const int64_t *row_ptr, const int32_t *col, const float *val,
                                   const int32_t *ids, int32_t k, float *C32, __nv_bfloat16 *C16,
-                                  int64_t ldc, cudaStream_t st);
+                                  int64_t ldc, double *sq, cudaStream_t st);
 
 // Per step: changed-cluster flags from the two assignments, cluster sizes, changed count.
 cudaError_t launch_changed(const int32_t *a_new, const int32_t *a_old, int64_t n_docs, int first,
@@ -141,12 +147,15 @@ struct UpdateArgs {
     void *CM;                  // compacted moved matrix (precision of the scored copy)
     int precision;
     int64_t ldc;
-    double *part_dot;          // sum_t S(t,j) * c_old(t,j)   (objective)
-    double *part_shift;        // sum_t (c_new - c_old)^2      (stop rule)
+    double *part_sq;           // sum_t c_new(t,j)^2 of the stored FP32 values
 };
 cudaError_t launch_update_norm(const UpdateArgs &u, cudaStream_t st);
 cudaError_t launch_update_write(const UpdateArgs &u, cudaStream_t st);
 int update_tile();   // largest moved-list tile of one update block
+// Zero the recomputed moved columns and fill the compacted matrix (see update.cu).
+cudaError_t launch_zero_moved(const int32_t *moved, const int32_t *sizes, int32_t n_moved, int32_t d,
+                              float *C32, __nv_bfloat16 *C16, void *CM, int precision, int64_t ldc,
+                              cudaStream_t st);
 cudaError_t launch_mdoc(const int32_t *a, const int32_t *pos_in_m, int64_t n, int32_t *mdoc,
                         cudaStream_t st);
 // Column sums over chunks in chunk order: out[m] = sum_c part[(tile*n_chunks + c)*m_tile + m].
@@ -155,10 +164,17 @@ cudaError_t launch_reduce_parts(const double *part, int32_t n_chunks, int32_t m_
 // inv_norm[m] = 1 / sqrt(normsq[m]) (0 for an empty sum).
 cudaError_t launch_inv_norm(const double *normsq, int32_t n_moved, double *inv_norm,
                             cudaStream_t st);
+// Per-document FP64 objective terms of moved clusters, summed per cluster in fixed point.
+cudaError_t launch_doc_obj(const int64_t *row_ptr, const int32_t *col, const float *val, int64_t n,
+                           const int32_t *a, const int32_t *mdoc, const float *C32, int64_t ldc,
+                           double scale, unsigned long long *dot_fx, cudaStream_t st);
 // Objective and shift of one step (single block, fixed order). See update.cu.
 cudaError_t launch_finish(const int32_t *pos_in_m, const int32_t *sizes, int32_t k,
-                          const double *dot, const double *normsq, const double *shift,
-                          double *norm_store, double *obj_out, double *shift_out,
+                          const unsigned long long *dot_fx, double inv_dot_scale, const double *normsq,
+                          const double *newsq, double *norm_store, double *sq_store, double *obj_out,
+                          double *shift_out, cudaStream_t st);
+// Squared norms of the stored FP32 columns.
+cudaError_t launch_col_sq(const float *C32, int64_t ldc, int32_t d, int32_t k, double *out,
                           cudaStream_t st);
 // FP32 -> BF16 (round to nearest even) of a d x ldc matrix.
 cudaError_t launch_to_bf16(const float *C32, __nv_bfloat16 *C16, int64_t n, cudaStream_t st);

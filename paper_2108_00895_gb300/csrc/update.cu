@@ -12,8 +12,11 @@
 //
 // Two passes over the postings: the first accumulates ||S_j||^2 (FP64, fixed term order
 // per chunk, chunks reduced in order), the second writes c = S / ||S|| into the FP32
-// master, the BF16 copy and the compacted moved-centroid matrix, and accumulates the
-// objective term S_j . c_j(old) and the squared shift ||c_j(new) - c_j(old)||^2.
+// master, the BF16 copy and the compacted moved-centroid matrix (after a store-only pass
+// that zeroes the moved columns), and accumulates the squared norm of the stored FP32
+// column (for the next step's shift). The objective term
+// S_j . c_j(old) comes from per-document FP64 dots against the old master (k_doc_obj),
+// summed per cluster in fixed point, before the update overwrites it.
 #include "skm_kernels.cuh"
 
 namespace skm {
@@ -55,6 +58,60 @@ cudaError_t launch_validate(const int64_t *row_ptr, const int32_t *col, const fl
     const int64_t threads = n_docs * 32;
     k_validate<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(row_ptr, col, val, n_docs,
                                                                   n_terms, err);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// Documents ordered by decreasing number of nonzeros (bucket sort; order within a bucket
+// is arbitrary and affects only scheduling): neighbouring warps of a scoring block then
+// carry similar work.
+// ------------------------------------------------------------------------------------
+constexpr int ORDER_BUCKETS = 4096;
+
+__global__ void k_len_hist(const int64_t *row_ptr, int64_t n, int32_t *hist) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t len = row_ptr[i + 1] - row_ptr[i];
+    atomicAdd(hist + (ORDER_BUCKETS - 1 - (int)min(len, (int64_t)ORDER_BUCKETS - 1)), 1);
+}
+
+__global__ void k_hist_scan(int32_t *hist) {   // one block of 1024 threads, exclusive scan
+    __shared__ int32_t part[1024];
+    constexpr int PER = ORDER_BUCKETS / 1024;
+    int loc[PER];
+    int s = 0;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) { loc[q] = hist[threadIdx.x * PER + q]; s += loc[q]; }
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const int v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int run = part[threadIdx.x] - s;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) { hist[threadIdx.x * PER + q] = run; run += loc[q]; }
+}
+
+__global__ void k_len_scatter(const int64_t *row_ptr, int64_t n, int32_t *offs, int32_t *order) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t len = row_ptr[i + 1] - row_ptr[i];
+    const int b = ORDER_BUCKETS - 1 - (int)min(len, (int64_t)ORDER_BUCKETS - 1);
+    order[atomicAdd(offs + b, 1)] = (int32_t)i;
+}
+
+cudaError_t launch_order_by_length(const int64_t *row_ptr, int64_t n, int32_t *hist, int32_t *order,
+                                   cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(hist, 0, ORDER_BUCKETS * sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    k_len_hist<<<blocks, 256, 0, st>>>(row_ptr, n, hist);
+    k_hist_scan<<<1, 1024, 0, st>>>(hist);
+    k_len_scatter<<<blocks, 256, 0, st>>>(row_ptr, n, hist, order);
     return cudaGetLastError();
 }
 
@@ -103,24 +160,29 @@ cudaError_t launch_csc_fill(const int64_t *row_ptr, const int32_t *col, const fl
 // ------------------------------------------------------------------------------------
 __global__ void k_init_centroids(const int64_t *row_ptr, const int32_t *col, const float *val,
                                  const int32_t *ids, int32_t k, float *C32, __nv_bfloat16 *C16,
-                                 int64_t ldc) {
+                                 int64_t ldc, double *sq) {
     const int lane = threadIdx.x & 31;
     const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (j >= k) return;
     const int64_t i = ids[j];
+    double s = 0.0;
     for (int64_t p = row_ptr[i] + lane; p < row_ptr[i + 1]; p += 32) {
         const int64_t o = (int64_t)col[p] * ldc + j;
         C32[o] = val[p];
         if (C16) C16[o] = __float2bfloat16_rn(val[p]);
+        s = fma((double)val[p], (double)val[p], s);
     }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(FULL, s, off);
+    if (lane == 0) sq[j] = s;
 }
 
 cudaError_t launch_init_centroids(const int64_t *row_ptr, const int32_t *col, const float *val,
                                   const int32_t *ids, int32_t k, float *C32, __nv_bfloat16 *C16,
-                                  int64_t ldc, cudaStream_t st) {
+                                  int64_t ldc, double *sq, cudaStream_t st) {
     const int64_t threads = (int64_t)k * 32;
     k_init_centroids<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(row_ptr, col, val, ids, k,
-                                                                        C32, C16, ldc);
+                                                                        C32, C16, ldc, sq);
     return cudaGetLastError();
 }
 
@@ -218,19 +280,28 @@ cudaError_t launch_compact_moved(const uint8_t *changed, int32_t k, int32_t *mov
 }
 
 // ------------------------------------------------------------------------------------
-// Update passes. Block = THREADS threads, one chunk of consecutive terms (blockIdx.x) and
-// one tile of the moved list (blockIdx.y). Thread tid owns the moved entries
-// m = tid + r * THREADS (r < R) of the tile: it zeroes and reads them, and keeps their
-// FP64 partial sums in registers, so the only cross-thread traffic is the integer
-// shared-memory atomics of the posting walk.
+// Update passes. One block per chunk of consecutive terms (blockIdx.x) and tile of the
+// moved list (blockIdx.y). Per term t:
+//   1. every posting (document i, value x) whose cluster is in the tile adds x * 2^F to
+//      acc[m] (64-bit integer atomics in shared memory: exact, order-independent); the
+//      thread whose add found acc[m] == 0 appends m to the term's touched list;
+//   2. each touched m is visited once: the norm pass adds S^2 to nrm[m], the write pass
+//      stores c = S / ||S_j|| into row t and adds c^2 to nrm[m] (squared norm of the
+//      stored FP32 column); acc[m] is reset to zero.
+// nrm[m] is a per-block FP64 sum over the block's terms in ascending order, written to
+// part[] at the end; chunks are then reduced in chunk order, so every sum is
+// deterministic. Entries of moved columns that no posting touches were zeroed before
+// (k_zero_moved), so the write pass only stores nonzeros.
 // ------------------------------------------------------------------------------------
-constexpr int UPD_THREADS = 512;
-constexpr int UPD_R = 8;                        // moved entries per thread per tile
-constexpr int UPD_TILE = UPD_THREADS * UPD_R;   // 4096 entries, 32 KiB of accumulators
+constexpr int UPD_THREADS = 1024;
+constexpr int UPD_TILE = 11264;   // 20 bytes of shared memory per entry: 225,280 bytes
 
 template <bool WRITE>
 __global__ void __launch_bounds__(UPD_THREADS) k_update(UpdateArgs u) {
-    extern __shared__ unsigned long long acc[];
+    extern __shared__ unsigned long long acc[];               // [m_tile]
+    double *nrm = reinterpret_cast<double *>(acc + u.m_tile);  // [m_tile]
+    int32_t *touched = reinterpret_cast<int32_t *>(nrm + u.m_tile);   // [m_tile]
+    __shared__ int32_t n_touched;
     const int tid = threadIdx.x;
     const int c = blockIdx.x;
     const int tile = blockIdx.y;
@@ -241,117 +312,61 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(UpdateArgs u) {
     const int32_t *__restrict__ row_idx = u.row_idx;
     const float *__restrict__ cval = u.cval;
     const int32_t *__restrict__ mdoc = u.mdoc;
-    float *__restrict__ C32 = u.C32;
     const double inv_scale = 1.0 / u.scale;
-    double p0[UPD_R], p1[UPD_R];
-#pragma unroll
-    for (int r = 0; r < UPD_R; ++r) {
-        p0[r] = 0.0;
-        p1[r] = 0.0;
+    for (int m = tid; m < mt; m += UPD_THREADS) {
+        acc[m] = 0ull;
+        nrm[m] = 0.0;
     }
+    if (tid == 0) n_touched = 0;
+    __syncthreads();
     const int32_t t0 = u.chunk_t0[c], t1 = u.chunk_t1[c];
     for (int32_t t = t0; t < t1; ++t) {
-#pragma unroll
-        for (int r = 0; r < UPD_R; ++r) {
-            const int m = tid + r * UPD_THREADS;
-            if (m < mt) acc[m] = 0ull;
-        }
-        __syncthreads();
         const int64_t pb = col_ptr[t], pe = col_ptr[t + 1];
         for (int64_t p = pb + tid; p < pe; p += UPD_THREADS) {
             const int mm = __ldg(mdoc + __ldg(row_idx + p)) - m0;
             if (mm >= 0 && mm < mt) {
                 const long long q = __double2ll_rn((double)__ldg(cval + p) * u.scale);
-                atomicAdd(acc + mm, (unsigned long long)q);
+                if (q != 0 && atomicAdd(acc + mm, (unsigned long long)q) == 0ull)
+                    touched[atomicAdd(&n_touched, 1)] = mm;
             }
         }
         __syncthreads();
+        const int nt = n_touched;
         const int64_t row = (int64_t)t * u.ldc;
-        if (!WRITE) {
-#pragma unroll
-            for (int r = 0; r < UPD_R; ++r) {
-                const int m = tid + r * UPD_THREADS;
-                if (m >= mt) continue;
-                const long long q = (long long)acc[m];
-                if (q != 0) {
-                    const double S = (double)q * inv_scale;
-                    p0[r] = fma(S, S, p0[r]);
-                }
-            }
-        } else {
-            // phase 1: all loads of the previous centroid values (independent, in flight
-            // together); phase 2: arithmetic and stores
-            float old[UPD_R];
-            int32_t jr[UPD_R];
-            bool live[UPD_R];
-#pragma unroll
-            for (int r = 0; r < UPD_R; ++r) {
-                const int m = tid + r * UPD_THREADS;
-                live[r] = m < mt;
-                jr[r] = live[r] ? __ldg(u.moved + m0 + m) : 0;
-                old[r] = live[r] ? C32[row + jr[r]] : 0.f;
-            }
-#pragma unroll
-            for (int r = 0; r < UPD_R; ++r) {
-                if (!live[r]) continue;
-                const int m = tid + r * UPD_THREADS;
-                const long long q = (long long)acc[m];
-                float cur = old[r];
-                if (__ldg(u.sizes + jr[r]) > 0) {     // an empty cluster keeps its centroid
-                    double cn = 0.0;
-                    if (q != 0) {
-                        const double S = (double)q * inv_scale;
-                        cn = S * __ldg(u.inv_norm + m0 + m);
-                        p0[r] = fma(S, (double)old[r], p0[r]);
-                    }
-                    if (q != 0 || old[r] != 0.f) {
-                        const double dlt = cn - (double)old[r];
-                        p1[r] = fma(dlt, dlt, p1[r]);
-                    }
-                    cur = (float)cn;
-                    C32[row + jr[r]] = cur;
-                    if (u.C16) u.C16[row + jr[r]] = __float2bfloat16_rn(cur);
-                }
+        for (int e = tid; e < nt; e += UPD_THREADS) {
+            const int m = touched[e];
+            const double S = (double)(long long)acc[m] * inv_scale;
+            acc[m] = 0ull;
+            if (!WRITE) {
+                nrm[m] = fma(S, S, nrm[m]);
+            } else {
+                const int32_t j = __ldg(u.moved + m0 + m);
+                if (__ldg(u.sizes + j) <= 0) continue;   // cannot happen: members give postings
+                const float cur = (float)(S * __ldg(u.inv_norm + m0 + m));
+                nrm[m] = fma((double)cur, (double)cur, nrm[m]);
+                u.C32[row + j] = cur;
+                if (u.C16) u.C16[row + j] = __float2bfloat16_rn(cur);
                 if (u.precision == 1)
                     reinterpret_cast<__nv_bfloat16 *>(u.CM)[row + m0 + m] = __float2bfloat16_rn(cur);
                 else
                     reinterpret_cast<float *>(u.CM)[row + m0 + m] = cur;
             }
         }
-        // the next term's zeroing touches only this thread's entries; the barrier after it
-        // orders it before any other thread's atomics
+        __syncthreads();
+        if (tid == 0) n_touched = 0;
+        __syncthreads();
     }
+    double *part = WRITE ? u.part_sq : u.part_norm;
     const int64_t ob = ((int64_t)tile * u.n_chunks + c) * u.m_tile;
-#pragma unroll
-    for (int r = 0; r < UPD_R; ++r) {
-        const int m = tid + r * UPD_THREADS;
-        if (m >= mt) continue;
-        if (!WRITE) {
-            u.part_norm[ob + m] = p0[r];
-        } else {
-            u.part_dot[ob + m] = p0[r];
-            u.part_shift[ob + m] = p1[r];
-        }
-    }
+    for (int m = tid; m < mt; m += UPD_THREADS) part[ob + m] = nrm[m];
 }
 
-// mdoc[i] = position of document i's cluster in the moved list (-1 if not moved).
-__global__ void k_mdoc(const int32_t *a, const int32_t *pos_in_m, int64_t n, int32_t *mdoc) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) mdoc[i] = pos_in_m[a[i]];
-}
-
-cudaError_t launch_mdoc(const int32_t *a, const int32_t *pos_in_m, int64_t n, int32_t *mdoc,
-                        cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    k_mdoc<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, pos_in_m, n, mdoc);
-    return cudaGetLastError();
-}
+static size_t update_smem(int m_tile) { return (size_t)m_tile * 20; }
 
 static cudaError_t launch_update(const UpdateArgs &u, bool write, cudaStream_t st) {
     if (u.n_chunks <= 0 || u.n_moved <= 0) return cudaSuccess;
     const int tiles = (u.n_moved + u.m_tile - 1) / u.m_tile;
-    const size_t smem = (size_t)u.m_tile * sizeof(unsigned long long);
+    const size_t smem = update_smem(u.m_tile);
     dim3 grid(u.n_chunks, tiles);
     cudaError_t e;
     if (write) {
@@ -374,6 +389,58 @@ cudaError_t launch_update_write(const UpdateArgs &u, cudaStream_t st) {
 }
 
 int update_tile() { return UPD_TILE; }
+
+// ------------------------------------------------------------------------------------
+// Moved columns before the write pass: a recomputed cluster's column is zeroed in the FP32
+// master and the BF16 copy (the write pass then stores its nonzeros); every compacted
+// column gets zero, or for a cluster left without members (which keeps its centroid) a
+// copy of the kept centroid. Store-only, one thread per (row, moved entry).
+// ------------------------------------------------------------------------------------
+__global__ void k_zero_moved(const int32_t *moved, const int32_t *sizes, int32_t n_moved, int32_t d,
+                             float *C32, __nv_bfloat16 *C16, void *CM, int precision, int64_t ldc) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n_moved) return;
+    const int32_t j = __ldg(moved + m);
+    const bool recomputed = __ldg(sizes + j) > 0;
+    for (int64_t t = blockIdx.y; t < d; t += gridDim.y) {
+        const int64_t row = t * ldc;
+        float cur = 0.f;
+        if (recomputed) {
+            C32[row + j] = 0.f;
+            if (C16) C16[row + j] = __float2bfloat16_rn(0.f);
+        } else {
+            cur = C32[row + j];
+        }
+        if (precision == 1)
+            reinterpret_cast<__nv_bfloat16 *>(CM)[row + m] = __float2bfloat16_rn(cur);
+        else
+            reinterpret_cast<float *>(CM)[row + m] = cur;
+    }
+}
+
+cudaError_t launch_zero_moved(const int32_t *moved, const int32_t *sizes, int32_t n_moved, int32_t d,
+                              float *C32, __nv_bfloat16 *C16, void *CM, int precision, int64_t ldc,
+                              cudaStream_t st) {
+    if (n_moved <= 0 || d <= 0) return cudaSuccess;
+    const unsigned bx = (unsigned)((n_moved + 255) / 256);
+    const unsigned by = (unsigned)min((int64_t)d, max((int64_t)1, (int64_t)152 * 64 / bx));
+    k_zero_moved<<<dim3(bx, by), 256, 0, st>>>(moved, sizes, n_moved, d, C32, C16, CM, precision, ldc);
+    return cudaGetLastError();
+}
+
+// mdoc[i] = position of document i's cluster in the moved list (-1 if not moved).
+__global__ void k_mdoc(const int32_t *a, const int32_t *pos_in_m, int64_t n, int32_t *mdoc) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) mdoc[i] = pos_in_m[a[i]];
+}
+
+cudaError_t launch_mdoc(const int32_t *a, const int32_t *pos_in_m, int64_t n, int32_t *mdoc,
+                        cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_mdoc<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, pos_in_m, n, mdoc);
+    return cudaGetLastError();
+}
+
 
 // Column sums over chunks, chunk order (deterministic).
 __global__ void k_reduce_parts(const double *part, int32_t n_chunks, int32_t m_tile,
@@ -407,14 +474,51 @@ cudaError_t launch_inv_norm(const double *normsq, int32_t n_moved, double *inv_n
 }
 
 // ------------------------------------------------------------------------------------
-// Objective of the step and max squared shift (single block, fixed order):
-//   objective = sum_j S_j . c_j(old) = sum_i x_i . c_{a_i}(old), where for a cluster that
-//   was not recomputed S_j . c_j = ||S_j|| (its centroid is S_j / ||S_j|| from the last
-//   update that recomputed it, and its members are unchanged since), kept in norm_store.
+// Objective terms: one warp per document of a moved cluster, FP64 dot x_i . c_{a_i}(old)
+// against the FP32 master (fixed butterfly reduction), added to its cluster's sum as a
+// 64-bit fixed-point integer (order-independent, so the sum is deterministic).
 // ------------------------------------------------------------------------------------
-__global__ void k_finish(const int32_t *pos_in_m, const int32_t *sizes, int32_t k, const double *dot,
-                         const double *normsq, const double *shift, double *norm_store,
-                         double *obj_out, double *shift_out) {
+__global__ void k_doc_obj(const int64_t *row_ptr, const int32_t *col, const float *val, int64_t n,
+                          const int32_t *a, const int32_t *mdoc, const float *C32, int64_t ldc,
+                          double scale, unsigned long long *dot_fx) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;
+    const int m = mdoc[i];
+    if (m < 0) return;
+    const int64_t j = a[i];
+    double acc = 0.0;
+    for (int64_t p = row_ptr[i] + lane; p < row_ptr[i + 1]; p += 32)
+        acc = fma((double)__ldg(val + p), (double)__ldg(C32 + (int64_t)__ldg(col + p) * ldc + j), acc);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(FULL, acc, off);
+    if (lane == 0) atomicAdd(dot_fx + m, (unsigned long long)__double2ll_rn(acc * scale));
+}
+
+cudaError_t launch_doc_obj(const int64_t *row_ptr, const int32_t *col, const float *val, int64_t n,
+                           const int32_t *a, const int32_t *mdoc, const float *C32, int64_t ldc,
+                           double scale, unsigned long long *dot_fx, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t threads = n * 32;
+    k_doc_obj<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(row_ptr, col, val, n, a, mdoc, C32, ldc,
+                                                                 scale, dot_fx);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// Objective of the step and max squared shift (single block, fixed order):
+//   objective = sum_j S_j . c_j(old) = sum_i x_i . c_{a_i}(old). For a moved cluster the
+//   term is the fixed-point sum of its documents' dots; for a cluster that was not
+//   recomputed it is ||S_j|| (its centroid is S_j / ||S_j|| from the last update that
+//   recomputed it, and its members are unchanged since), kept in norm_store.
+//   shift_j = ||c_new||^2 + ||c_old||^2 - 2 c_new . c_old with ||c_new|| = 1 (FP64 before
+//   rounding), ||c_old||^2 the stored FP32 column's squared norm, and
+//   c_new . c_old = (S_j . c_old) / ||S_j||.
+// ------------------------------------------------------------------------------------
+__global__ void k_finish(const int32_t *pos_in_m, const int32_t *sizes, int32_t k,
+                         const unsigned long long *dot_fx, double inv_dot_scale, const double *normsq,
+                         const double *newsq, double *norm_store, double *sq_store, double *obj_out,
+                         double *shift_out) {
     __shared__ double so[1024];
     __shared__ double sm[1024];
     double o = 0.0, mx = 0.0;
@@ -422,9 +526,13 @@ __global__ void k_finish(const int32_t *pos_in_m, const int32_t *sizes, int32_t 
         const int m = pos_in_m[j];
         if (sizes[j] <= 0) continue;
         if (m >= 0) {
-            o += dot[m];
-            if (shift[m] > mx) mx = shift[m];
-            norm_store[j] = sqrt(normsq[m]);
+            const double dot = (double)(long long)dot_fx[m] * inv_dot_scale;
+            const double nrm = sqrt(normsq[m]);
+            o += dot;
+            const double sh = 1.0 + sq_store[j] - 2.0 * dot / nrm;
+            if (sh > mx) mx = sh;
+            norm_store[j] = nrm;
+            sq_store[j] = newsq[m];
         } else {
             o += norm_store[j];
         }
@@ -446,11 +554,30 @@ __global__ void k_finish(const int32_t *pos_in_m, const int32_t *sizes, int32_t 
 }
 
 cudaError_t launch_finish(const int32_t *pos_in_m, const int32_t *sizes, int32_t k,
-                          const double *dot, const double *normsq, const double *shift,
-                          double *norm_store, double *obj_out, double *shift_out,
+                          const unsigned long long *dot_fx, double inv_dot_scale, const double *normsq,
+                          const double *newsq, double *norm_store, double *sq_store, double *obj_out,
+                          double *shift_out, cudaStream_t st) {
+    k_finish<<<1, 1024, 0, st>>>(pos_in_m, sizes, k, dot_fx, inv_dot_scale, normsq, newsq, norm_store,
+                                 sq_store, obj_out, shift_out);
+    return cudaGetLastError();
+}
+
+// Squared norms of the stored FP32 columns: out[j] = sum_t C32[t, j]^2 (one thread per
+// column, rows in order; used after centroids are loaded from outside).
+__global__ void k_col_sq(const float *C32, int64_t ldc, int32_t d, int32_t k, double *out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= k) return;
+    double s = 0.0;
+    for (int32_t t = 0; t < d; ++t) {
+        const double v = (double)C32[(int64_t)t * ldc + j];
+        s = fma(v, v, s);
+    }
+    out[j] = s;
+}
+
+cudaError_t launch_col_sq(const float *C32, int64_t ldc, int32_t d, int32_t k, double *out,
                           cudaStream_t st) {
-    k_finish<<<1, 1024, 0, st>>>(pos_in_m, sizes, k, dot, normsq, shift, norm_store, obj_out,
-                                 shift_out);
+    k_col_sq<<<(k + 127) / 128, 128, 0, st>>>(C32, ldc, d, k, out);
     return cudaGetLastError();
 }
 
