@@ -250,7 +250,7 @@ skm_status stage_docs(skm_ctx *ctx, const skm_csr *docs, DevCsr &out) {
         out.val = P<float>(ctx->d_val);
     }
     SKM_TRY(reset_counters(ctx));
-    SKM_CUDA(launch_validate(out.row_ptr, out.col, out.val, out.n, out.d,
+    SKM_CUDA(launch_validate(out.row_ptr, out.col, out.val, out.n, out.nnz, out.d,
                              P<int32_t>(ctx->counters) + CNT_ERR, ctx->st));
     ctx->stats.launches_total++;
     SKM_TRY(read_counters(ctx));
@@ -261,7 +261,7 @@ skm_status stage_docs(skm_ctx *ctx, const skm_csr *docs, DevCsr &out) {
         if (e & 2) why += " value negative or not finite;";
         if (e & 4) why += " empty row;";
         if (e & 8) why += " row L2 norm not within 1e-5 of 1;";
-        if (e & 16) why += " row_ptr not monotone;";
+        if (e & 16) why += " row offsets outside [0, nnz] or decreasing;";
         return fail(ctx, SKM_ERR_INVALID, "invalid documents:%s", why.c_str());
     }
     return SKM_OK;

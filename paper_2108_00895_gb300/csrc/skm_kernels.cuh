@@ -94,9 +94,10 @@ cudaError_t launch_partition(const PartitionArgs &a, cudaStream_t st);
 // ---------------------------------------------------------------- update (update.cu)
 // Input validation of a CSR collection; sets bits in *err:
 //   1 column out of range or not strictly increasing, 2 value negative or not finite,
-//   4 empty row, 8 row norm not within 1e-5 of 1, 16 row_ptr not monotone.
+//   4 empty row, 8 row norm not within 1e-5 of 1, 16 row offsets not within [0, nnz] or
+//   decreasing (such a row is not read).
 cudaError_t launch_validate(const int64_t *row_ptr, const int32_t *col, const float *val,
-                            int64_t n_docs, int32_t n_terms, int32_t *err, cudaStream_t st);
+                            int64_t n_docs, int64_t nnz, int32_t n_terms, int32_t *err, cudaStream_t st);
 
 // order[] = document ids by decreasing number of nonzeros; hist is scratch of 4096 ints.
 cudaError_t launch_order_by_length(const int64_t *row_ptr, int64_t n, int32_t *hist, int32_t *order,

@@ -25,16 +25,18 @@ namespace skm {
 // Validation: one warp per row.
 // ------------------------------------------------------------------------------------
 __global__ void k_validate(const int64_t *row_ptr, const int32_t *col, const float *val,
-                           int64_t n_docs, int32_t n_terms, int32_t *err) {
+                           int64_t n_docs, int64_t nnz, int32_t n_terms, int32_t *err) {
     const int lane = threadIdx.x & 31;
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= n_docs) return;
     const int64_t beg = row_ptr[i], end = row_ptr[i + 1];
     int e = 0;
-    if (end < beg) e |= 16;
+    // a row outside [0, nnz] is flagged and not read, so bad offsets cannot fault
+    const bool in_bounds = beg >= 0 && end <= nnz && beg <= end;
+    if (!in_bounds) e |= 16;
     if (end == beg) e |= 4;
     double ss = 0.0;
-    if (end > beg) {
+    if (in_bounds && end > beg) {
         for (int64_t p = beg + lane; p < end; p += 32) {
             const int32_t t = col[p];
             if (t < 0 || t >= n_terms) e |= 1;
@@ -53,10 +55,10 @@ __global__ void k_validate(const int64_t *row_ptr, const int32_t *col, const flo
 }
 
 cudaError_t launch_validate(const int64_t *row_ptr, const int32_t *col, const float *val,
-                            int64_t n_docs, int32_t n_terms, int32_t *err, cudaStream_t st) {
+                            int64_t n_docs, int64_t nnz, int32_t n_terms, int32_t *err, cudaStream_t st) {
     if (n_docs <= 0) return cudaSuccess;
     const int64_t threads = n_docs * 32;
-    k_validate<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(row_ptr, col, val, n_docs,
+    k_validate<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(row_ptr, col, val, n_docs, nnz,
                                                                   n_terms, err);
     return cudaGetLastError();
 }

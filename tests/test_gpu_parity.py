@@ -265,6 +265,11 @@ def test_invalid_inputs_are_rejected(skm):
         with pytest.raises(skm.SkmError) as e:
             km.fit(bad, np.arange(5))
         assert "norm" in str(e.value)
+        bad = synth.Csr(docs.row_ptr.copy(), docs.col_idx, docs.values, docs.n_terms)
+        bad.row_ptr[5] = docs.nnz + 100          # offsets past the arrays are flagged, not read
+        with pytest.raises(skm.SkmError) as e:
+            km.fit(bad, np.arange(5))
+        assert e.value.status == skm.SKM_ERR_INVALID and "offsets" in str(e.value)
         # the context is still usable after rejected calls
         r = km.fit(docs, np.arange(5))
         assert r.iters >= 1
