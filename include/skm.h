@@ -175,6 +175,40 @@ SKM_API skm_status skm_get_stats(const skm_ctx *ctx, skm_stats *out);
 /* Device bytes currently held by the context. */
 SKM_API size_t skm_mem_used(const skm_ctx *ctx);
 
+/*
+ * Assignment step that allocates no device memory. The paper has no counterpart: this is a
+ * service of the library for callers that cannot let a library allocate -- callers whose
+ * device memory is owned by another allocator (a framework's pool, or a fixed per-process
+ * budget), or that must not trigger an allocation (which can synchronise the device) where
+ * they call. Every input and output comes from the caller; the only scratch (per-slice
+ * candidate lists and validation flags) is one fixed 32 MiB device array inside the library,
+ * which every GPU that loads the library holds until the process exits. No cudaMalloc,
+ * cudaFree or allocating library routine is called.
+ *
+ * Result: for each document the centroid of largest FP32 similarity (nonzeros summed in CSR
+ * order with fused multiply-adds), ties to the lowest index -- what skm_assign returns for an
+ * FP32 context with rescore = 0.
+ *   docs        device CSR (on_device must be 1), checked as in skm_assign.
+ *   k           number of centroids, >= 1.
+ *   centroids   device float[n_terms * ld], term-major, 16-byte aligned: entry (t, j) is
+ *               centroids[t * ld + j]; ld >= k and a multiple of 256 (columns k..ld-1 are
+ *               read and ignored).
+ *   assign_out  device int32[n_docs]; score_out device float[n_docs] (the FP32 similarity of
+ *               the chosen centroid) or NULL.
+ *   stream      cudaStream_t to run on (NULL = legacy default stream); the call returns after
+ *               its work on the stream has finished.
+ * Limit: n_docs * ceil(k / 256) <= 1,048,568 (32 bytes of scratch per document and 256-column
+ * slice); a larger request returns SKM_ERR_BUDGET before any GPU work.
+ * Errors: SKM_ERR_INVALID for bad arguments or documents, SKM_ERR_CUDA for a CUDA failure.
+ * The first call on a device looks up the scratch array's device address (once per device,
+ * with that device current); make that first call before any stream capture on the device.
+ * All calls share the one scratch array, which keeps the last call's contents: calls that
+ * overlap on the GPU (from several streams or threads) race, so the caller must serialise them.
+ */
+SKM_API skm_status skm_assign_fixed_scratch(const skm_csr *docs, int32_t k, const float *centroids,
+                                            int64_t ld, int32_t *assign_out, float *score_out,
+                                            void *stream);
+
 #ifdef __cplusplus
 }
 #endif

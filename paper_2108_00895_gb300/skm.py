@@ -64,7 +64,11 @@ class skm_stats(ctypes.Structure):
 
 EXPORTS = ("skm_config_default", "skm_create", "skm_destroy", "skm_last_error", "skm_fit",
            "skm_assign", "skm_update", "skm_set_centroids", "skm_get_centroids", "skm_n_terms",
-           "skm_get_stats", "skm_mem_used")
+           "skm_get_stats", "skm_mem_used", "skm_assign_fixed_scratch")
+
+# skm_assign_fixed_scratch: capacity of its fixed scratch, in (document x 256-column slice) units
+FIXED_SCRATCH_SLICE = 256
+FIXED_SCRATCH_UNITS = 1_048_568
 
 
 def load(build_if_missing: bool = True):
@@ -94,6 +98,8 @@ def load(build_if_missing: bool = True):
             "skm_n_terms": (ctypes.c_int32, [P]),
             "skm_get_stats": (st, [P, ctypes.POINTER(skm_stats)]),
             "skm_mem_used": (ctypes.c_size_t, [P]),
+            "skm_assign_fixed_scratch": (st, [ctypes.POINTER(skm_csr), ctypes.c_int32, P, ctypes.c_int64,
+                                              P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -201,6 +207,16 @@ def skm_set_centroids(ctx, n_terms: int, centroids, on_device: int) -> None:
 
 def skm_get_centroids(ctx, out, on_device: int) -> None:
     _check(ctx, load().skm_get_centroids(ctx, _ptr(out), int(on_device)))
+
+
+def skm_assign_fixed_scratch(csr: skm_csr, k: int, centroids, ld: int, assign_out, score_out=None,
+                             stream: int | None = None) -> None:
+    """FP32 assignment without any device allocation (see include/skm.h): every buffer is the
+    caller's, the scratch is a fixed array inside the library. Device tensors only."""
+    st = load().skm_assign_fixed_scratch(ctypes.byref(csr), int(k), _ptr(centroids), int(ld),
+                                         _ptr(assign_out), _ptr(score_out), stream or None)
+    if st != SKM_OK:
+        raise SkmError(st, "skm_assign_fixed_scratch failed")
 
 
 def skm_get_stats(ctx) -> skm_stats:
