@@ -38,7 +38,7 @@ __device__ __forceinline__ void fma_row(float2 (&acc)[NV * 16 / (int)sizeof(CT) 
 // row segment is one coalesced 512-byte warp access. The document's (t, x) pairs are read
 // 32 at a time and broadcast by shuffle.
 // ------------------------------------------------------------------------------------
-template <typename CT, int NV>
+template <typename CT, int NV, bool COLLECT>
 __global__ void __launch_bounds__(256) k_score(ScoreArgs a) {
     constexpr int EPV = 16 / (int)sizeof(CT);   // elements per 16-byte vector
     constexpr int J = NV * EPV;                  // columns per lane
@@ -89,31 +89,50 @@ __global__ void __launch_bounds__(256) k_score(ScoreArgs a) {
         }
     }
 
-    float ls[TOPT];
-    int lj[TOPT];
+    if constexpr (COLLECT) {
+        // same scores as the top-list pass; append every one at or above the threshold
+        const float thr = a.thr[pos];
 #pragma unroll
-    for (int q = 0; q < TOPT; ++q) { ls[q] = -INFINITY; lj[q] = INT32_MAX; }
+        for (int u = 0; u < NV; ++u) {
 #pragma unroll
-    for (int u = 0; u < NV; ++u) {
-#pragma unroll
-        for (int e = 0; e < EPV; ++e) {
-            const int64_t c = j0 + u * 32 * EPV + lane * EPV + e;
-            if (c < a.ncols) {
-                const int id = a.col_ids ? __ldg(a.col_ids + c) : (int)c;
+            for (int e = 0; e < EPV; ++e) {
+                const int64_t c = j0 + u * 32 * EPV + lane * EPV + e;
                 const int qq = (u * EPV + e) >> 1;
-                topt_insert(ls, lj, (e & 1) ? acc[qq].y : acc[qq].x, id);
+                const float sc = (e & 1) ? acc[qq].y : acc[qq].x;
+                if (c < a.ncols && sc >= thr) {
+                    const int id = a.col_ids ? __ldg(a.col_ids + c) : (int)c;
+                    const int at = atomicAdd(a.cand_cnt + pos, 1);
+                    if (at < a.cap) a.cand[(int64_t)pos * a.cap + at] = id;
+                }
             }
         }
-    }
-    topt_warp_merge(ls, lj);
-    if (lane < TOPT) {
-        float s = ls[0];
-        int j = lj[0];
+    } else {
+        float ls[TOPT];
+        int lj[TOPT];
 #pragma unroll
-        for (int q = 1; q < TOPT; ++q) if (lane == q) { s = ls[q]; j = lj[q]; }
-        const int64_t o = ((int64_t)slice * a.n_list + pos) * TOPT + lane;
-        a.part_s[o] = s;
-        a.part_j[o] = j;
+        for (int q = 0; q < TOPT; ++q) { ls[q] = -INFINITY; lj[q] = INT32_MAX; }
+#pragma unroll
+        for (int u = 0; u < NV; ++u) {
+#pragma unroll
+            for (int e = 0; e < EPV; ++e) {
+                const int64_t c = j0 + u * 32 * EPV + lane * EPV + e;
+                if (c < a.ncols) {
+                    const int id = a.col_ids ? __ldg(a.col_ids + c) : (int)c;
+                    const int qq = (u * EPV + e) >> 1;
+                    topt_insert(ls, lj, (e & 1) ? acc[qq].y : acc[qq].x, id);
+                }
+            }
+        }
+        topt_warp_merge(ls, lj);
+        if (lane < TOPT) {
+            float s = ls[0];
+            int j = lj[0];
+#pragma unroll
+            for (int q = 1; q < TOPT; ++q) if (lane == q) { s = ls[q]; j = lj[q]; }
+            const int64_t o = ((int64_t)slice * a.n_list + pos) * TOPT + lane;
+            a.part_s[o] = s;
+            a.part_j[o] = j;
+        }
     }
 }
 
@@ -130,27 +149,39 @@ int slice_width(int precision, int k) {
     return k <= 256 ? 256 : 512;
 }
 
-cudaError_t launch_score(const ScoreArgs &a, int precision, int slice_cols, cudaStream_t st) {
+template <bool COLLECT>
+static cudaError_t launch_score_t(const ScoreArgs &a, int precision, int slice_cols, cudaStream_t st) {
     if (a.n_list <= 0) return cudaSuccess;
     const int n_slices = (a.ncols + slice_cols - 1) / slice_cols;
     if (n_slices <= 0) return cudaSuccess;
     dim3 grid((a.n_list + 7) / 8, n_slices);
     if (precision == 0) {
         switch (slice_cols) {
-            case 128: k_score<float, 1><<<grid, 256, 0, st>>>(a); break;
-            case 256: k_score<float, 2><<<grid, 256, 0, st>>>(a); break;
-            case 512: k_score<float, 4><<<grid, 256, 0, st>>>(a); break;
+            case 128: k_score<float, 1, COLLECT><<<grid, 256, 0, st>>>(a); break;
+            case 256: k_score<float, 2, COLLECT><<<grid, 256, 0, st>>>(a); break;
+            case 512: k_score<float, 4, COLLECT><<<grid, 256, 0, st>>>(a); break;
             default: return cudaErrorInvalidValue;
         }
     } else {
         switch (slice_cols) {
-            case 256: k_score<__nv_bfloat16, 1><<<grid, 256, 0, st>>>(a); break;
-            case 512: k_score<__nv_bfloat16, 2><<<grid, 256, 0, st>>>(a); break;
-            case 1024: k_score<__nv_bfloat16, 4><<<grid, 256, 0, st>>>(a); break;
+            case 256: k_score<__nv_bfloat16, 1, COLLECT><<<grid, 256, 0, st>>>(a); break;
+            case 512: k_score<__nv_bfloat16, 2, COLLECT><<<grid, 256, 0, st>>>(a); break;
+            case 1024: k_score<__nv_bfloat16, 4, COLLECT><<<grid, 256, 0, st>>>(a); break;
             default: return cudaErrorInvalidValue;
         }
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_score(const ScoreArgs &a, int precision, int slice_cols, cudaStream_t st) {
+    return launch_score_t<false>(a, precision, slice_cols, st);
+}
+
+// Collect pass: the scoring pass again (bit-identical scores) for documents whose
+// candidate set did not fit in the top list; appends every centroid at or above the
+// document's threshold.
+cudaError_t launch_collect(const ScoreArgs &a, int precision, int slice_cols, cudaStream_t st) {
+    return launch_score_t<true>(a, precision, slice_cols, st);
 }
 
 // ------------------------------------------------------------------------------------
@@ -226,6 +257,17 @@ __global__ void k_decide(DecideArgs a) {
     const float rho = fmaxf(fmaxf(ls[1], tail), rbound);
 
     int64_t nnz = a.row_ptr[i + 1] - a.row_ptr[i];
+    if (s1 <= 0.f && rho <= 0.f) {
+        // every score is exactly zero: the document shares no term with any centroid's
+        // support (scores are sums of non-negative products), so every exact score is zero
+        // and the lowest index, centroid 0, is the argmax
+        a.a_new[i] = 0;
+        a.s_state[i] = 0.f;
+        a.r_state[i] = 0.f;
+        a.clean[i] = 1;
+        if (a.score_out) a.score_out[i] = 0.f;
+        return;
+    }
     const double beta = score_beta(a.precision, nnz);
     const double tau_i = fmax((double)a.tau, 2.0 * beta * fmax((double)s1, 0.0) / (1.0 - beta));
     const bool accept = !a.rescore || ((double)s1 - (double)rho > tau_i);
@@ -259,8 +301,10 @@ __global__ void k_decide(DecideArgs a) {
         atomicAdd(a.counters64 + C64_NNZ_REFULL, (unsigned long long)nnz);
         return;   // state untouched: the refull pass decides it as an unpruned document
     }
-    const int q = atomicAdd(&a.counters[CNT_FULL64], 1);
-    a.full64_doc[q] = i;
+    // more candidates than the list holds: collect them all (threshold rounded down)
+    const int q = atomicAdd(&a.counters[CNT_COLLECT], 1);
+    a.collect_doc[q] = i;
+    a.collect_thr[q] = __double2float_rd(thr);
     a.a_new[i] = j1;
     a.s_state[i] = s1;
     a.r_state[i] = rho;
@@ -282,14 +326,22 @@ cudaError_t launch_decide(const DecideArgs &a, cudaStream_t st) {
 __global__ void k_rescore64(RescoreArgs a) {
     const int lane = threadIdx.x & 31;
     const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int n = *a.count;
+    const int n = a.count ? *a.count : a.n_fixed;
     if (q >= n) return;
     const int32_t i = a.rs_doc[q];
+    int n_cand = a.stride;
+    if (a.cand_cnt) {
+        n_cand = a.cand_cnt[q];
+        if (n_cand > a.stride) {          // list overflowed: FP64 against all k instead
+            if (lane == 0) a.full64_doc[atomicAdd(a.full64_count, 1)] = i;
+            return;
+        }
+    }
     const int64_t beg = a.row_ptr[i], end = a.row_ptr[i + 1];
     double best = -INFINITY;
     int bj = INT32_MAX;
-    for (int c = 0; c < TOPT; ++c) {
-        const int j = a.rs_cand[(int64_t)q * TOPT + c];
+    for (int c = 0; c < n_cand; ++c) {
+        const int j = a.rs_cand[(int64_t)q * a.stride + c];
         if (j < 0) continue;
         double acc = 0.0;
         for (int64_t p = beg + lane; p < end; p += 32)

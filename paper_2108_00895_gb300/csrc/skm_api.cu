@@ -58,7 +58,7 @@ struct skm_ctx {
     // per-document state
     Buf abuf[2], s_state, r_state, clean, mdoc, order, order_hist;
     Buf part_s, part_j;
-    Buf list_a, list_b, rs_doc, rs_cand, refull, full64;
+    Buf list_a, list_b, rs_doc, rs_cand, refull, full64, collect_doc, collect_thr, cand, cand_cnt;
     // per-cluster state
     Buf changed, sizes, moved, pos_in_m, normsq, inv_norm, dot_fx, newsq;
     Buf part_norm, part_sq;
@@ -74,6 +74,9 @@ struct skm_ctx {
 };
 
 namespace {
+
+constexpr int kCollectCap = 64;          // candidates kept per document by the collect pass
+constexpr int64_t kCollectBatch = 65536; // documents per collect launch
 
 skm_status fail(skm_ctx *c, skm_status s, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
 skm_status fail(skm_ctx *c, skm_status s, const char *fmt, ...) {
@@ -322,6 +325,10 @@ skm_status ensure_doc_bufs(skm_ctx *ctx, int64_t n) {
     SKM_TRY(ensure(ctx, ctx->rs_cand, sizeof(int32_t) * n * TOPT));
     SKM_TRY(ensure(ctx, ctx->refull, sizeof(int32_t) * n));
     SKM_TRY(ensure(ctx, ctx->full64, sizeof(int32_t) * n));
+    SKM_TRY(ensure(ctx, ctx->collect_doc, sizeof(int32_t) * n));
+    SKM_TRY(ensure(ctx, ctx->collect_thr, sizeof(float) * n));
+    SKM_TRY(ensure(ctx, ctx->cand, sizeof(int32_t) * (size_t)std::min<int64_t>(n, kCollectBatch) * kCollectCap));
+    SKM_TRY(ensure(ctx, ctx->cand_cnt, sizeof(int32_t) * (size_t)std::min<int64_t>(n, kCollectBatch)));
     return SKM_OK;
 }
 
@@ -452,6 +459,8 @@ skm_status score_and_decide(skm_ctx *ctx, const DevCsr &dc, const int32_t *list,
     da.rs_cand = P<int32_t>(ctx->rs_cand);
     da.refull_doc = P<int32_t>(ctx->refull);
     da.full64_doc = P<int32_t>(ctx->full64);
+    da.collect_doc = P<int32_t>(ctx->collect_doc);
+    da.collect_thr = P<float>(ctx->collect_thr);
     {
         Timed tm(ctx, ctx->ev_decide);
         SKM_CUDA(launch_decide(da, ctx->st));
@@ -465,22 +474,60 @@ skm_status score_and_decide(skm_ctx *ctx, const DevCsr &dc, const int32_t *list,
 skm_status rescore_queues(skm_ctx *ctx, const DevCsr &dc, int32_t *a_new, float *score_out) {
     SKM_TRY(read_counters(ctx));
     const int n_rs = ctx->h_counters[CNT_RESCORE];
-    const int n_f64 = ctx->h_counters[CNT_FULL64];
+    const int n_col = ctx->h_counters[CNT_COLLECT];
+    RescoreArgs ra{};
+    ra.row_ptr = dc.row_ptr;
+    ra.col = dc.col;
+    ra.val = dc.val;
+    ra.C32 = P<float>(ctx->C32);
+    ra.ldc = ctx->ldc;
+    ra.a_new = a_new;
+    ra.score_out = score_out;
+    ra.full64_doc = P<int32_t>(ctx->full64);
+    ra.full64_count = P<int32_t>(ctx->counters) + CNT_FULL64;
     if (n_rs > 0) {
-        RescoreArgs ra{};
+        // candidate lists of the decision (at most TOPT each)
         ra.count = P<int32_t>(ctx->counters) + CNT_RESCORE;
         ra.rs_doc = P<int32_t>(ctx->rs_doc);
         ra.rs_cand = P<int32_t>(ctx->rs_cand);
-        ra.row_ptr = dc.row_ptr;
-        ra.col = dc.col;
-        ra.val = dc.val;
-        ra.C32 = P<float>(ctx->C32);
-        ra.ldc = ctx->ldc;
-        ra.a_new = a_new;
-        ra.score_out = score_out;
+        ra.stride = TOPT;
+        ra.cand_cnt = nullptr;
         Timed tm(ctx, ctx->ev_decide);
         SKM_CUDA(launch_rescore64(ra, n_rs, ctx->st));
         ctx->stats.launches_total++;
+    }
+    for (int64_t b0 = 0; b0 < n_col; b0 += kCollectBatch) {
+        // more candidates than the list held: collect them all, then rescore those
+        const int32_t nb = (int32_t)std::min<int64_t>(kCollectBatch, n_col - b0);
+        Timed tm(ctx, ctx->ev_decide);
+        SKM_CUDA(cudaMemsetAsync(ctx->cand_cnt.p, 0, sizeof(int32_t) * nb, ctx->st));
+        ScoreArgs sa{};
+        sa.row_ptr = dc.row_ptr;
+        sa.col = dc.col;
+        sa.val = dc.val;
+        sa.doc_list = P<int32_t>(ctx->collect_doc) + b0;
+        sa.n_list = nb;
+        sa.C = ctx->cfg.precision == SKM_BF16 ? ctx->C16.p : ctx->C32.p;
+        sa.ldc = ctx->ldc;
+        sa.ncols = ctx->cfg.k;
+        sa.thr = P<float>(ctx->collect_thr) + b0;
+        sa.cand_cnt = P<int32_t>(ctx->cand_cnt);
+        sa.cand = P<int32_t>(ctx->cand);
+        sa.cap = kCollectCap;
+        SKM_CUDA(launch_collect(sa, ctx->cfg.precision, ctx->slice, ctx->st));
+        ra.count = nullptr;
+        ra.n_fixed = nb;
+        ra.rs_doc = sa.doc_list;
+        ra.rs_cand = sa.cand;
+        ra.stride = kCollectCap;
+        ra.cand_cnt = sa.cand_cnt;
+        SKM_CUDA(launch_rescore64(ra, nb, ctx->st));
+        ctx->stats.launches_total += 2;
+    }
+    int n_f64 = 0;
+    if (n_col > 0) {
+        SKM_TRY(read_counters(ctx));
+        n_f64 = ctx->h_counters[CNT_FULL64];
     }
     if (n_f64 > 0) {
         Full64Args fa{};
@@ -498,7 +545,7 @@ skm_status rescore_queues(skm_ctx *ctx, const DevCsr &dc, int32_t *a_new, float 
         SKM_CUDA(launch_full64(fa, n_f64, ctx->st));
         ctx->stats.launches_total++;
     }
-    ctx->stats.docs_rescored += n_rs;
+    ctx->stats.docs_rescored += n_rs + n_col - n_f64;
     ctx->stats.docs_rescored_full += n_f64;
     return SKM_OK;
 }
@@ -639,7 +686,8 @@ skm_status skm_destroy(skm_ctx *ctx) {
                   &ctx->d_val, &ctx->col_ptr, &ctx->row_idx, &ctx->cval, &ctx->tcount, &ctx->chunk_t0,
                   &ctx->chunk_t1, &ctx->abuf[0], &ctx->abuf[1], &ctx->s_state, &ctx->r_state,
                   &ctx->clean, &ctx->mdoc, &ctx->order, &ctx->order_hist, &ctx->part_s, &ctx->part_j, &ctx->list_a, &ctx->list_b, &ctx->rs_doc,
-                  &ctx->rs_cand, &ctx->refull, &ctx->full64, &ctx->changed, &ctx->sizes, &ctx->moved,
+                  &ctx->rs_cand, &ctx->refull, &ctx->full64, &ctx->collect_doc, &ctx->collect_thr, &ctx->cand,
+                  &ctx->cand_cnt, &ctx->changed, &ctx->sizes, &ctx->moved,
                   &ctx->pos_in_m, &ctx->normsq, &ctx->inv_norm, &ctx->dot_fx, &ctx->newsq,
                   &ctx->part_norm, &ctx->part_sq, &ctx->sq_store, &ctx->counters, &ctx->counters64, &ctx->scal,
                   &ctx->obj, &ctx->init_ids};

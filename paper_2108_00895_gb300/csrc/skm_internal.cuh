@@ -95,10 +95,17 @@ struct ScoreArgs {
     const int32_t *col_ids;    // nullable: column -> centroid id (compacted matrices)
     float *part_s;
     int32_t *part_j;
+    // collect mode only: every centroid with score >= thr[pos] is appended to
+    // cand[pos * cap + c] (c < cap); cand_cnt[pos] counts them all
+    const float *thr;
+    int32_t *cand_cnt;
+    int32_t *cand;
+    int32_t cap;
 };
 
 // Launch helpers (defined in assign.cu). Return cudaSuccess or the launch error.
 cudaError_t launch_score(const ScoreArgs &a, int precision, int slice_cols, cudaStream_t st);
+cudaError_t launch_collect(const ScoreArgs &a, int precision, int slice_cols, cudaStream_t st);
 int slice_width(int precision, int k);   // KS for the scoring kernel
 
 }  // namespace skm

@@ -15,7 +15,8 @@ enum {
     CNT_CHANGED = 5,  // documents whose assignment changed in this step
     CNT_MOVED = 6,    // centroids in the moved list
     CNT_ERR = 7,      // validation error flags (bitmask)
-    CNT_N = 8
+    CNT_COLLECT = 8,  // documents queued for the collect pass
+    CNT_N = 9
 };
 // 64-bit device counters (nonzeros of listed documents, for the work counts).
 enum { C64_NNZ_PRUNED = 0, C64_NNZ_REFULL = 1, C64_N = 2 };
@@ -44,12 +45,19 @@ struct DecideArgs {
     int32_t *rs_cand;          // rescore queue: TOPT candidates each (-1 = none)
     int32_t *refull_doc;
     int32_t *full64_doc;
+    int32_t *collect_doc;      // collect queue: document ids
+    float *collect_thr;        // collect queue: score threshold (rounded down)
 };
 
 struct RescoreArgs {
-    const int32_t *count;
+    const int32_t *count;       // device count of queue entries, or NULL to use n_fixed
+    int32_t n_fixed;
     const int32_t *rs_doc;
-    const int32_t *rs_cand;
+    const int32_t *rs_cand;     // [queue position][stride] candidate ids (-1 = none)
+    int32_t stride;
+    const int32_t *cand_cnt;    // nullable: number of candidates per position (collect lists)
+    int32_t *full64_doc;        // overflowing collect lists are appended here
+    int32_t *full64_count;
     const int64_t *row_ptr;
     const int32_t *col;
     const float *val;

@@ -98,6 +98,46 @@ def test_assign_ties_go_to_lowest_index(skm):
         assert (a != 5).all()
 
 
+@pytest.mark.parametrize("copies", [9, 70])
+def test_assign_many_near_ties_collect_and_full_fp64(skm, copies):
+    """More tied candidates than the top list holds: 9 copies go through the collect pass,
+    70 copies exceed its capacity and go to FP64 scoring against all k."""
+    docs = _corpus(400, 600, 20, 3, 60, 1.1, 14)
+    rng = np.random.default_rng(15)
+    k = copies + 20
+    C = (rng.random((600, k)) * 0.05).astype(np.float32)
+    strong = rng.random(600).astype(np.float32)
+    for q in range(copies):
+        C[:, 10 + q] = strong
+    C /= np.linalg.norm(C, axis=0, keepdims=True)
+    for prec in ("fp32", "bf16"):
+        with skm.SphericalKMeans(k, precision=prec) as km:
+            km.set_centroids(C)
+            a, _ = km.assign(docs)
+            st = km.stats()
+        a_or, _, _ = oracle.assign(docs, C)
+        np.testing.assert_array_equal(a, a_or)
+        assert st["docs_rescored"] + st["docs_rescored_full"] > 0
+        if copies > 64:
+            assert st["docs_rescored_full"] > 0
+
+
+def test_assign_documents_sharing_no_term_with_any_centroid(skm):
+    """All scores zero: every exact score is zero and centroid 0 (lowest index) wins."""
+    docs = _corpus(300, 800, 15, 3, 40, 1.1, 16)
+    rng = np.random.default_rng(17)
+    C = rng.random((800, 12)).astype(np.float32)
+    used = np.unique(docs.col_idx[docs.row_ptr[5]:docs.row_ptr[6]])
+    C[used, :] = 0.0                        # document 5 overlaps no centroid
+    C /= np.linalg.norm(C, axis=0, keepdims=True)
+    with skm.SphericalKMeans(12, precision="bf16") as km:
+        km.set_centroids(C)
+        a, s = km.assign(docs)
+    a_or, s1, _ = oracle.assign(docs, C)
+    assert s1[5] == 0.0 and a[5] == 0 and s[5] == 0.0
+    _check_assign(docs, C, a)
+
+
 def test_assign_device_buffers(skm):
     import torch
     docs = _corpus(500, 2000, 30, 5, 200, 1.1, 12)
