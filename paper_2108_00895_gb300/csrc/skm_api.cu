@@ -54,14 +54,14 @@ struct skm_ctx {
     // staged documents (host inputs are copied here)
     Buf d_row_ptr, d_col, d_val;
     // transposed postings
-    Buf col_ptr, row_idx, cval, tcount, chunk_t0, chunk_t1;
+    Buf col_ptr, row_idx, cval, pterm, tcount, light_t0, light_t1, heavy_terms;
     // per-document state
     Buf abuf[2], s_state, r_state, clean, mdoc, order, order_hist;
     Buf part_s, part_j;
     Buf list_a, list_b, rs_doc, rs_cand, refull, full64, collect_doc, collect_thr, cand, cand_cnt;
     // per-cluster state
     Buf changed, sizes, moved, pos_in_m, normsq, inv_norm, dot_fx, newsq;
-    Buf part_norm, part_sq;
+    Buf normsq128, sq128;
     Buf counters, counters64, scal, obj, init_ids;
     int32_t *h_counters = nullptr;  // pinned mirror
     unsigned long long *h_counters64 = nullptr;
@@ -332,19 +332,22 @@ skm_status ensure_doc_bufs(skm_ctx *ctx, int64_t n) {
     return SKM_OK;
 }
 
-// Term-major postings of the staged documents and the update work list.
+// Term-major postings of the staged documents and the update work lists.
 struct Postings {
-    int32_t n_chunks = 0;
-    double scale = 0;
-    int64_t d_eff = 0;   // terms with at least one posting
+    int32_t n_light = 0;   // chunks of consecutive light terms
+    int32_t n_heavy = 0;   // terms with more postings than a chunk holds
+    int F = 0;             // fixed-point bits of the update sums
+    int64_t d_eff = 0;     // terms with at least one posting
 };
 
 skm_status build_postings(skm_ctx *ctx, const DevCsr &dc, Postings &pg) {
     const int32_t d = dc.d;
+    const int32_t k = ctx->cfg.k;
     SKM_TRY(ensure(ctx, ctx->tcount, sizeof(int32_t) * (d + 1)));
     SKM_TRY(ensure(ctx, ctx->col_ptr, sizeof(int64_t) * (d + 1)));
     SKM_TRY(ensure(ctx, ctx->row_idx, sizeof(int32_t) * dc.nnz));
     SKM_TRY(ensure(ctx, ctx->cval, sizeof(float) * dc.nnz));
+    SKM_TRY(ensure(ctx, ctx->pterm, sizeof(int32_t) * dc.nnz));
     SKM_CUDA(cudaMemsetAsync(ctx->tcount.p, 0, sizeof(int32_t) * (d + 1), ctx->st));
     SKM_CUDA(launch_term_count(dc.col, dc.nnz, P<int32_t>(ctx->tcount), ctx->st));
     ctx->stats.launches_total++;
@@ -353,50 +356,62 @@ skm_status build_postings(skm_ctx *ctx, const DevCsr &dc, Postings &pg) {
     SKM_TRY(sync(ctx));
     std::vector<int64_t> cp(d + 1);
     cp[0] = 0;
-    int64_t max_df = 1;
     pg.d_eff = 0;
     for (int32_t t = 0; t < d; ++t) {
         cp[t + 1] = cp[t] + cnt[t];
-        max_df = std::max<int64_t>(max_df, cnt[t]);
         pg.d_eff += cnt[t] > 0;
     }
-    // Fixed point: every value is <= 1 + 1e-5, a sum has at most max_df terms.
+    // Fixed point: a posting value is at most 1 + 1e-5 and a sum has at most N of them, so
+    // with 2^bits > N every sum stays below 2^62 and ||S||^2 below 2^124.
     int bits = 0;
-    while ((int64_t(1) << bits) < max_df + 1) ++bits;
-    const int F = 61 - bits;
-    pg.scale = std::ldexp(1.0, F);
-    // Work list: every term belongs to one chunk; chunks balance postings plus a per-term
-    // row cost, heavy terms alone.
-    const int64_t target = std::max<int64_t>(4096, (dc.nnz + (int64_t)d * 8) / 304 + 1);
-    std::vector<int32_t> t0, t1;
+    while ((int64_t(1) << bits) < dc.n + 1) ++bits;
+    pg.F = 61 - bits;
+    // light chunks: consecutive terms with at most `chunk` postings in all; the term span of a
+    // chunk is capped so that (term offset, moved position) packs into 32 bits
+    const int64_t chunk = update_chunk_postings();
+    const int64_t span_cap = std::max<int64_t>(1, std::min<int64_t>(4096, (int64_t(0xffffffff) / std::max(k, 1))));
+    std::vector<int32_t> l0, l1, heavy;
     int64_t w = 0;
-    int32_t start = 0;
-    for (int32_t t = 0; t < d; ++t) {
-        w += cnt[t] + 8;
-        if (w >= target || t == d - 1) {
-            t0.push_back(start);
-            t1.push_back(t + 1);
-            start = t + 1;
-            w = 0;
+    int32_t start = -1, last = -1;
+    auto close = [&](int32_t end) {
+        if (start >= 0) {
+            l0.push_back(start);
+            l1.push_back(end);
         }
+        start = -1;
+        w = 0;
+    };
+    for (int32_t t = 0; t < d; ++t) {
+        if (cnt[t] > chunk) {          // a chunk's posting range never spans a heavy term
+            close(t);
+            heavy.push_back(t);
+            continue;
+        }
+        if (cnt[t] == 0) continue;
+        if (start >= 0 && (w + cnt[t] > chunk || t - start >= span_cap)) close(t);
+        if (start < 0) start = t;
+        w += cnt[t];
+        last = t;
     }
-    pg.n_chunks = (int32_t)t0.size();
-    SKM_TRY(ensure(ctx, ctx->chunk_t0, sizeof(int32_t) * pg.n_chunks));
-    SKM_TRY(ensure(ctx, ctx->chunk_t1, sizeof(int32_t) * pg.n_chunks));
+    if (start >= 0) close(last + 1);
+    pg.n_light = (int32_t)l0.size();
+    pg.n_heavy = (int32_t)heavy.size();
+    SKM_TRY(ensure(ctx, ctx->light_t0, sizeof(int32_t) * std::max(pg.n_light, 1)));
+    SKM_TRY(ensure(ctx, ctx->light_t1, sizeof(int32_t) * std::max(pg.n_light, 1)));
+    SKM_TRY(ensure(ctx, ctx->heavy_terms, sizeof(int32_t) * std::max(pg.n_heavy, 1)));
     SKM_CUDA(cudaMemcpyAsync(ctx->col_ptr.p, cp.data(), sizeof(int64_t) * (d + 1), cudaMemcpyHostToDevice, ctx->st));
-    SKM_CUDA(cudaMemcpyAsync(ctx->chunk_t0.p, t0.data(), sizeof(int32_t) * pg.n_chunks, cudaMemcpyHostToDevice, ctx->st));
-    SKM_CUDA(cudaMemcpyAsync(ctx->chunk_t1.p, t1.data(), sizeof(int32_t) * pg.n_chunks, cudaMemcpyHostToDevice, ctx->st));
+    if (pg.n_light)
+        SKM_CUDA(cudaMemcpyAsync(ctx->light_t0.p, l0.data(), sizeof(int32_t) * pg.n_light, cudaMemcpyHostToDevice, ctx->st));
+    if (pg.n_light)
+        SKM_CUDA(cudaMemcpyAsync(ctx->light_t1.p, l1.data(), sizeof(int32_t) * pg.n_light, cudaMemcpyHostToDevice, ctx->st));
+    if (pg.n_heavy)
+        SKM_CUDA(cudaMemcpyAsync(ctx->heavy_terms.p, heavy.data(), sizeof(int32_t) * pg.n_heavy, cudaMemcpyHostToDevice, ctx->st));
     SKM_CUDA(cudaMemsetAsync(ctx->tcount.p, 0, sizeof(int32_t) * (d + 1), ctx->st));
-    SKM_CUDA(launch_csc_fill(dc.row_ptr, dc.col, dc.val, dc.n, P<int64_t>(ctx->col_ptr),
-                             P<int32_t>(ctx->tcount), P<int32_t>(ctx->row_idx), P<float>(ctx->cval), ctx->st));
+    SKM_CUDA(launch_csc_fill(dc.row_ptr, dc.col, dc.val, dc.n, P<int64_t>(ctx->col_ptr), P<int32_t>(ctx->tcount),
+                             P<int32_t>(ctx->row_idx), P<float>(ctx->cval), P<int32_t>(ctx->pterm), ctx->st));
     ctx->stats.launches_total++;
-    // partial-sum buffers of the update passes
-    const int tile = update_tile();
-    const int32_t k = ctx->cfg.k;
-    const int64_t tiles = (k + tile - 1) / tile;
-    const size_t parts = (size_t)tiles * pg.n_chunks * tile;
-    SKM_TRY(ensure(ctx, ctx->part_norm, sizeof(double) * parts));
-    SKM_TRY(ensure(ctx, ctx->part_sq, sizeof(double) * parts));
+    SKM_TRY(ensure(ctx, ctx->normsq128, 2 * sizeof(unsigned long long) * k));
+    SKM_TRY(ensure(ctx, ctx->sq128, 2 * sizeof(unsigned long long) * k));
     // the transient host vectors must outlive the async copies
     SKM_TRY(sync(ctx));
     return SKM_OK;
@@ -581,37 +596,37 @@ skm_status update_step(skm_ctx *ctx, const DevCsr &dc, const Postings &pg, const
                                 P<float>(ctx->C32), ctx->ldc, dot_scale,
                                 P<unsigned long long>(ctx->dot_fx), ctx->st));
         UpdateArgs u{};
-        u.n_chunks = pg.n_chunks;
-        u.chunk_t0 = P<int32_t>(ctx->chunk_t0);
-        u.chunk_t1 = P<int32_t>(ctx->chunk_t1);
+        u.n_light = pg.n_light;
+        u.light_t0 = P<int32_t>(ctx->light_t0);
+        u.light_t1 = P<int32_t>(ctx->light_t1);
+        u.n_heavy = pg.n_heavy;
+        u.heavy_terms = P<int32_t>(ctx->heavy_terms);
         u.col_ptr = P<int64_t>(ctx->col_ptr);
         u.row_idx = P<int32_t>(ctx->row_idx);
         u.cval = P<float>(ctx->cval);
-        u.a = a_new;
+        u.pterm = P<int32_t>(ctx->pterm);
         u.mdoc = P<int32_t>(ctx->mdoc);
         u.moved = P<int32_t>(ctx->moved);
-        u.pos_in_m = P<int32_t>(ctx->pos_in_m);
         u.n_moved = n_moved;
-        u.sizes = P<int32_t>(ctx->sizes);
-        const int tile = update_tile();
-        const int tiles = (n_moved + tile - 1) / tile;
-        u.m_tile = ((n_moved + tiles - 1) / tiles + 31) & ~31;
-        u.scale = pg.scale;
-        u.part_norm = P<double>(ctx->part_norm);
+        u.F = pg.F;
+        u.inv_scale = std::ldexp(1.0, -pg.F);
+        u.normsq128 = P<unsigned long long>(ctx->normsq128);
+        u.sq128 = P<unsigned long long>(ctx->sq128);
         u.inv_norm = P<double>(ctx->inv_norm);
         u.C32 = P<float>(ctx->C32);
         u.C16 = ctx->cfg.precision == SKM_BF16 ? P<__nv_bfloat16>(ctx->C16) : nullptr;
         u.CM = ctx->CM.p;
         u.precision = ctx->cfg.precision;
         u.ldc = ctx->ldc;
-        u.part_sq = P<double>(ctx->part_sq);
+        SKM_CUDA(cudaMemsetAsync(u.normsq128, 0, 2 * sizeof(unsigned long long) * n_moved, ctx->st));
+        SKM_CUDA(cudaMemsetAsync(u.sq128, 0, 2 * sizeof(unsigned long long) * n_moved, ctx->st));
         SKM_CUDA(launch_update_norm(u, ctx->st));
-        SKM_CUDA(launch_reduce_parts(u.part_norm, pg.n_chunks, u.m_tile, n_moved, P<double>(ctx->normsq), ctx->st));
-        SKM_CUDA(launch_inv_norm(P<double>(ctx->normsq), n_moved, P<double>(ctx->inv_norm), ctx->st));
-        SKM_CUDA(launch_zero_moved(u.moved, u.sizes, n_moved, ctx->d, u.C32, u.C16, u.CM, u.precision, u.ldc,
-                                   ctx->st));
+        SKM_CUDA(launch_from_u128(u.normsq128, nullptr, n_moved, pg.F, P<double>(ctx->normsq), P<double>(ctx->inv_norm),
+                                  nullptr, ctx->st));
+        SKM_CUDA(launch_zero_moved(u.moved, P<int32_t>(ctx->sizes), n_moved, ctx->d, u.C32, u.C16, u.CM, u.precision,
+                                   u.ldc, ctx->st));
         SKM_CUDA(launch_update_write(u, ctx->st));
-        SKM_CUDA(launch_reduce_parts(u.part_sq, pg.n_chunks, u.m_tile, n_moved, P<double>(ctx->newsq), ctx->st));
+        SKM_CUDA(launch_from_u128(nullptr, u.sq128, n_moved, pg.F, nullptr, nullptr, P<double>(ctx->newsq), ctx->st));
         ctx->stats.launches_total += 8;
     }
     // with no moved cluster pos_in_m is -1 everywhere and the objective is sum_j ||S_j||
@@ -683,13 +698,13 @@ skm_status skm_destroy(skm_ctx *ctx) {
     DeviceGuard g(ctx->cfg.device);
     cudaStreamSynchronize(ctx->st);
     Buf *all[] = {&ctx->C32, &ctx->C16, &ctx->CM, &ctx->norm_store, &ctx->d_row_ptr, &ctx->d_col,
-                  &ctx->d_val, &ctx->col_ptr, &ctx->row_idx, &ctx->cval, &ctx->tcount, &ctx->chunk_t0,
-                  &ctx->chunk_t1, &ctx->abuf[0], &ctx->abuf[1], &ctx->s_state, &ctx->r_state,
+                  &ctx->d_val, &ctx->col_ptr, &ctx->row_idx, &ctx->cval, &ctx->pterm, &ctx->tcount,
+                  &ctx->light_t0, &ctx->light_t1, &ctx->heavy_terms, &ctx->abuf[0], &ctx->abuf[1], &ctx->s_state, &ctx->r_state,
                   &ctx->clean, &ctx->mdoc, &ctx->order, &ctx->order_hist, &ctx->part_s, &ctx->part_j, &ctx->list_a, &ctx->list_b, &ctx->rs_doc,
                   &ctx->rs_cand, &ctx->refull, &ctx->full64, &ctx->collect_doc, &ctx->collect_thr, &ctx->cand,
                   &ctx->cand_cnt, &ctx->changed, &ctx->sizes, &ctx->moved,
                   &ctx->pos_in_m, &ctx->normsq, &ctx->inv_norm, &ctx->dot_fx, &ctx->newsq,
-                  &ctx->part_norm, &ctx->part_sq, &ctx->sq_store, &ctx->counters, &ctx->counters64, &ctx->scal,
+                  &ctx->normsq128, &ctx->sq128, &ctx->sq_store, &ctx->counters, &ctx->counters64, &ctx->scal,
                   &ctx->obj, &ctx->init_ids};
     for (Buf *b : all) release(ctx, *b);
     if (ctx->h_counters) cudaFreeHost(ctx->h_counters);

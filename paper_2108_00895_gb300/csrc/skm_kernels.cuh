@@ -115,7 +115,7 @@ cudaError_t launch_order_by_length(const int64_t *row_ptr, int64_t n, int32_t *h
 cudaError_t launch_term_count(const int32_t *col, int64_t nnz, int32_t *cnt, cudaStream_t st);
 cudaError_t launch_csc_fill(const int64_t *row_ptr, const int32_t *col, const float *val,
                             int64_t n_docs, const int64_t *col_ptr, int32_t *fill,
-                            int32_t *row_idx, float *cval, cudaStream_t st);
+                            int32_t *row_idx, float *cval, int32_t *pterm, cudaStream_t st);
 
 // Initial centroids c_j = x_{ids[j]} (the matrices must be zero beforehand); sq[j] gets
 // the squared norm of the stored column.
@@ -132,47 +132,42 @@ cudaError_t launch_compact_moved(const uint8_t *changed, int32_t k, int32_t *mov
                                  int32_t *pos_in_m, int32_t *counters, cudaStream_t st);
 
 struct UpdateArgs {
-    // work list: chunk c covers terms [chunk_t0[c], chunk_t1[c])
-    int32_t n_chunks;
-    const int32_t *chunk_t0;
-    const int32_t *chunk_t1;
+    // light chunks: chunk c covers terms [light_t0[c], light_t1[c]); heavy terms one by one
+    int32_t n_light;
+    const int32_t *light_t0;
+    const int32_t *light_t1;
+    int32_t n_heavy;
+    const int32_t *heavy_terms;
     const int64_t *col_ptr;
-    const int32_t *row_idx;
-    const float *cval;
-    const int32_t *a;          // assignment of this step
+    const int32_t *row_idx;    // document of each posting
+    const float *cval;         // value of each posting
+    const int32_t *pterm;      // term of each posting
     const int32_t *mdoc;       // per document: moved-list position of its cluster, or -1
     const int32_t *moved;      // M
-    const int32_t *pos_in_m;
     int32_t n_moved;
-    const int32_t *sizes;      // members per cluster
-    int32_t m_tile;            // moved entries per tile (grid.y = tiles)
-    double scale;              // fixed-point scale 2^F
-    // norm pass output: part[(tile * n_chunks + c) * m_tile + m]
-    double *part_norm;
-    // write pass
+    int F;                     // fixed-point bits: S is in units of 2^-F
+    double inv_scale;          // 2^-F
+    unsigned long long *normsq128;  // [n_moved][2] norm pass output (units 2^-2F)
+    unsigned long long *sq128;      // [n_moved][2] write pass output (units 2^-62)
     const double *inv_norm;    // [n_moved]
     float *C32;
     __nv_bfloat16 *C16;        // nullable (FP32 mode)
     void *CM;                  // compacted moved matrix (precision of the scored copy)
     int precision;
     int64_t ldc;
-    double *part_sq;           // sum_t c_new(t,j)^2 of the stored FP32 values
 };
 cudaError_t launch_update_norm(const UpdateArgs &u, cudaStream_t st);
 cudaError_t launch_update_write(const UpdateArgs &u, cudaStream_t st);
-int update_tile();   // largest moved-list tile of one update block
+int update_chunk_postings();   // most postings of a light chunk
+// normsq, inv_norm (nullable source normsq128) and newsq (nullable source sq128).
+cudaError_t launch_from_u128(const unsigned long long *normsq128, const unsigned long long *sq128, int32_t n,
+                             int F, double *normsq, double *inv_norm, double *newsq, cudaStream_t st);
 // Zero the recomputed moved columns and fill the compacted matrix (see update.cu).
 cudaError_t launch_zero_moved(const int32_t *moved, const int32_t *sizes, int32_t n_moved, int32_t d,
                               float *C32, __nv_bfloat16 *C16, void *CM, int precision, int64_t ldc,
                               cudaStream_t st);
 cudaError_t launch_mdoc(const int32_t *a, const int32_t *pos_in_m, int64_t n, int32_t *mdoc,
                         cudaStream_t st);
-// Column sums over chunks in chunk order: out[m] = sum_c part[(tile*n_chunks + c)*m_tile + m].
-cudaError_t launch_reduce_parts(const double *part, int32_t n_chunks, int32_t m_tile,
-                                int32_t n_moved, double *out, cudaStream_t st);
-// inv_norm[m] = 1 / sqrt(normsq[m]) (0 for an empty sum).
-cudaError_t launch_inv_norm(const double *normsq, int32_t n_moved, double *inv_norm,
-                            cudaStream_t st);
 // Per-document FP64 objective terms of moved clusters, summed per cluster in fixed point.
 cudaError_t launch_doc_obj(const int64_t *row_ptr, const int32_t *col, const float *val, int64_t n,
                            const int32_t *a, const int32_t *mdoc, const float *C32, int64_t ldc,

@@ -10,11 +10,10 @@
 // their postings: the update is deterministic without a sort of the postings. The rows of
 // the term-major centroid matrix are then written with coalesced stores.
 //
-// Two passes over the postings: the first accumulates ||S_j||^2 (FP64, fixed term order
-// per chunk, chunks reduced in order), the second writes c = S / ||S|| into the FP32
-// master, the BF16 copy and the compacted moved-centroid matrix (after a store-only pass
-// that zeroes the moved columns), and accumulates the squared norm of the stored FP32
-// column (for the next step's shift). The objective term
+// Two passes over the postings: the first accumulates ||S_j||^2 (exact 128-bit integer),
+// the second writes c = S / ||S|| into the FP32 master, the BF16 copy and the compacted
+// moved-centroid matrix (after a store-only pass that zeroes the moved columns), and
+// accumulates the squared norm of the stored FP32 column (for the next step's shift). The objective term
 // S_j . c_j(old) comes from per-document FP64 dots against the old master (k_doc_obj),
 // summed per cluster in fixed point, before the update overwrites it.
 #include "skm_kernels.cuh"
@@ -135,7 +134,7 @@ cudaError_t launch_term_count(const int32_t *col, int64_t nnz, int32_t *cnt, cud
 
 __global__ void k_csc_fill(const int64_t *row_ptr, const int32_t *col, const float *val,
                            int64_t n_docs, const int64_t *col_ptr, int32_t *fill,
-                           int32_t *row_idx, float *cval) {
+                           int32_t *row_idx, float *cval, int32_t *pterm) {
     const int lane = threadIdx.x & 31;
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= n_docs) return;
@@ -144,16 +143,17 @@ __global__ void k_csc_fill(const int64_t *row_ptr, const int32_t *col, const flo
         const int64_t o = col_ptr[t] + atomicAdd(fill + t, 1);
         row_idx[o] = (int32_t)i;
         cval[o] = val[p];
+        pterm[o] = t;
     }
 }
 
 cudaError_t launch_csc_fill(const int64_t *row_ptr, const int32_t *col, const float *val,
                             int64_t n_docs, const int64_t *col_ptr, int32_t *fill,
-                            int32_t *row_idx, float *cval, cudaStream_t st) {
+                            int32_t *row_idx, float *cval, int32_t *pterm, cudaStream_t st) {
     if (n_docs <= 0) return cudaSuccess;
     const int64_t threads = n_docs * 32;
     k_csc_fill<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(row_ptr, col, val, n_docs, col_ptr,
-                                                                  fill, row_idx, cval);
+                                                                  fill, row_idx, cval, pterm);
     return cudaGetLastError();
 }
 
@@ -282,115 +282,203 @@ cudaError_t launch_compact_moved(const uint8_t *changed, int32_t k, int32_t *mov
 }
 
 // ------------------------------------------------------------------------------------
-// Update passes. One block per chunk of consecutive terms (blockIdx.x) and tile of the
-// moved list (blockIdx.y). Per term t:
-//   1. every posting (document i, value x) whose cluster is in the tile adds x * 2^F to
-//      acc[m] (64-bit integer atomics in shared memory: exact, order-independent); the
-//      thread whose add found acc[m] == 0 appends m to the term's touched list;
-//   2. each touched m is visited once: the norm pass adds S^2 to nrm[m], the write pass
-//      stores c = S / ||S_j|| into row t and adds c^2 to nrm[m] (squared norm of the
-//      stored FP32 column); acc[m] is reset to zero.
-// nrm[m] is a per-block FP64 sum over the block's terms in ascending order, written to
-// part[] at the end; chunks are then reduced in chunk order, so every sum is
-// deterministic. Entries of moved columns that no posting touches were zeroed before
-// (k_zero_moved), so the write pass only stores nonzeros.
+// Update passes. Both passes compute, for every (term t, moved cluster m) with a posting,
+// the exact fixed-point sum S(t, m) = sum of round(x * 2^F) over the postings of t whose
+// document is in cluster m (64-bit integer additions: exact and order-independent).
+//   norm pass:  ||S_m||^2 += S(t, m)^2, as a 128-bit integer (exact, order-independent);
+//   write pass: c = S(t, m) 2^-F / ||S_m|| is stored into row t of the FP32 master, the BF16
+//               copy and the compacted matrix, and sum_t c^2 of the stored FP32 values is
+//               accumulated as a 128-bit fixed-point integer (scale 2^62).
+// Every sum is exact or integer, so the update is deterministic without ordering work.
+// Light terms (at most UPD_CHUNK postings) are packed into chunks of consecutive terms; a
+// block reduces a chunk with a shared-memory hash table keyed by (term, cluster) and one
+// barrier. Heavy terms get one block each with a dense shared accumulator over the moved
+// list (tiled when the list exceeds UPD_TILE).
 // ------------------------------------------------------------------------------------
-constexpr int UPD_THREADS = 1024;
-constexpr int UPD_TILE = 11264;   // 20 bytes of shared memory per entry: 225,280 bytes
+constexpr int UPD_CHUNK = 4096;               // postings per light chunk (table half full)
+constexpr int UPD_SLOTS = 2 * UPD_CHUNK;      // hash table slots
+constexpr uint32_t UPD_EMPTY = 0xffffffffu;
+constexpr int UPD_LIGHT_THREADS = 512;
+constexpr int UPD_HEAVY_THREADS = 1024;
+constexpr int UPD_TILE = 16384;               // moved entries per heavy-term tile (12 bytes each)
+
+// round(x * 2^F) for a finite x >= 0 from its bits (integer arithmetic only; ties round up)
+__device__ __forceinline__ unsigned long long fixed_point(float x, int F) {
+    const uint32_t b = __float_as_uint(x);
+    const int e = (int)(b >> 23);
+    if (e == 0 && (b & 0x7fffffu) == 0) return 0ull;
+    const unsigned long long mant = (unsigned long long)((b & 0x7fffffu) | (e ? 0x800000u : 0u));
+    const int sh = (e ? e : 1) - 150 + F;      // x = mant * 2^((e ? e : 1) - 150)
+    if (sh >= 0) return mant << sh;
+    if (sh <= -25) return 0ull;
+    return (mant + (1ull << (-sh - 1))) >> (-sh);
+}
+
+// acc (two 64-bit words, low first) += x (hi:lo); order-independent exact 128-bit sum
+__device__ __forceinline__ void atomic_add_u128(unsigned long long *acc, unsigned long long lo,
+                                                unsigned long long hi) {
+    const unsigned long long old = atomicAdd(acc, lo);
+    hi += (old + lo < old) ? 1ull : 0ull;
+    if (hi) atomicAdd(acc + 1, hi);
+}
+
+// S (fixed point, 2^-F units) of entry m of term t: the norm or write step.
+template <bool WRITE>
+__device__ __forceinline__ void update_entry(const UpdateArgs &u, int32_t t, int m, unsigned long long S) {
+    if (!WRITE) {
+        atomic_add_u128(u.normsq128 + 2 * m, S * S, __umul64hi(S, S));
+        return;
+    }
+    const int32_t j = __ldg(u.moved + m);
+    const float c = (float)((double)S * u.inv_scale * __ldg(u.inv_norm + m));
+    const int64_t row = (int64_t)t * u.ldc;
+    u.C32[row + j] = c;
+    if (u.C16) u.C16[row + j] = __float2bfloat16_rn(c);
+    if (u.precision == 1)
+        reinterpret_cast<__nv_bfloat16 *>(u.CM)[row + m] = __float2bfloat16_rn(c);
+    else
+        reinterpret_cast<float *>(u.CM)[row + m] = c;
+    const double c2 = (double)c * (double)c;   // exact (24-bit mantissa squared)
+    const unsigned long long q = (unsigned long long)__double2ull_rn(ldexp(c2, 62));
+    atomic_add_u128(u.sq128 + 2 * m, q, 0ull);
+}
 
 template <bool WRITE>
-__global__ void __launch_bounds__(UPD_THREADS) k_update(UpdateArgs u) {
-    extern __shared__ unsigned long long acc[];               // [m_tile]
-    double *nrm = reinterpret_cast<double *>(acc + u.m_tile);  // [m_tile]
-    int32_t *touched = reinterpret_cast<int32_t *>(nrm + u.m_tile);   // [m_tile]
-    __shared__ int32_t n_touched;
-    const int tid = threadIdx.x;
-    const int c = blockIdx.x;
-    const int tile = blockIdx.y;
-    const int m0 = tile * u.m_tile;
-    const int mt = min(u.m_tile, u.n_moved - m0);
-    if (mt <= 0) return;
-    const int64_t *__restrict__ col_ptr = u.col_ptr;
-    const int32_t *__restrict__ row_idx = u.row_idx;
-    const float *__restrict__ cval = u.cval;
-    const int32_t *__restrict__ mdoc = u.mdoc;
-    const double inv_scale = 1.0 / u.scale;
-    for (int m = tid; m < mt; m += UPD_THREADS) {
-        acc[m] = 0ull;
-        nrm[m] = 0.0;
+__global__ void __launch_bounds__(UPD_LIGHT_THREADS) k_upd_light(UpdateArgs u) {
+    extern __shared__ unsigned long long vals[];                         // [UPD_SLOTS]
+    uint32_t *keys = reinterpret_cast<uint32_t *>(vals + UPD_SLOTS);     // [UPD_SLOTS]
+    for (int q = threadIdx.x; q < UPD_SLOTS; q += UPD_LIGHT_THREADS) {
+        keys[q] = UPD_EMPTY;
+        vals[q] = 0ull;
     }
-    if (tid == 0) n_touched = 0;
     __syncthreads();
-    const int32_t t0 = u.chunk_t0[c], t1 = u.chunk_t1[c];
-    for (int32_t t = t0; t < t1; ++t) {
-        const int64_t pb = col_ptr[t], pe = col_ptr[t + 1];
-        for (int64_t p = pb + tid; p < pe; p += UPD_THREADS) {
-            const int mm = __ldg(mdoc + __ldg(row_idx + p)) - m0;
-            if (mm >= 0 && mm < mt) {
-                const long long q = __double2ll_rn((double)__ldg(cval + p) * u.scale);
-                if (q != 0 && atomicAdd(acc + mm, (unsigned long long)q) == 0ull)
-                    touched[atomicAdd(&n_touched, 1)] = mm;
+    const uint32_t nm = (uint32_t)u.n_moved;
+    for (int c = blockIdx.x; c < u.n_light; c += gridDim.x) {
+        const int32_t t0 = u.light_t0[c], t1 = u.light_t1[c];
+        const int64_t pb = u.col_ptr[t0], pe = u.col_ptr[t1];
+        for (int64_t p = pb + threadIdx.x; p < pe; p += UPD_LIGHT_THREADS) {
+            const int m = __ldg(u.mdoc + __ldg(u.row_idx + p));
+            if (m < 0) continue;
+            const unsigned long long q = fixed_point(__ldg(u.cval + p), u.F);
+            if (q == 0ull) continue;
+            const uint32_t key = (uint32_t)(__ldg(u.pterm + p) - t0) * nm + (uint32_t)m;
+            uint32_t h = (key * 2654435761u) >> (32 - 13);          // UPD_SLOTS = 2^13
+            while (true) {
+                const uint32_t prev = atomicCAS(keys + h, UPD_EMPTY, key);
+                if (prev == UPD_EMPTY || prev == key) {
+                    atomicAdd(vals + h, q);
+                    break;
+                }
+                h = (h + 1) & (UPD_SLOTS - 1);
             }
         }
         __syncthreads();
-        const int nt = n_touched;
-        const int64_t row = (int64_t)t * u.ldc;
-        for (int e = tid; e < nt; e += UPD_THREADS) {
-            const int m = touched[e];
-            const double S = (double)(long long)acc[m] * inv_scale;
-            acc[m] = 0ull;
-            if (!WRITE) {
-                nrm[m] = fma(S, S, nrm[m]);
-            } else {
-                const int32_t j = __ldg(u.moved + m0 + m);
-                if (__ldg(u.sizes + j) <= 0) continue;   // cannot happen: members give postings
-                const float cur = (float)(S * __ldg(u.inv_norm + m0 + m));
-                nrm[m] = fma((double)cur, (double)cur, nrm[m]);
-                u.C32[row + j] = cur;
-                if (u.C16) u.C16[row + j] = __float2bfloat16_rn(cur);
-                if (u.precision == 1)
-                    reinterpret_cast<__nv_bfloat16 *>(u.CM)[row + m0 + m] = __float2bfloat16_rn(cur);
-                else
-                    reinterpret_cast<float *>(u.CM)[row + m0 + m] = cur;
-            }
+        for (int q = threadIdx.x; q < UPD_SLOTS; q += UPD_LIGHT_THREADS) {
+            const uint32_t key = keys[q];
+            if (key == UPD_EMPTY) continue;
+            const uint32_t tl = key / nm;
+            update_entry<WRITE>(u, t0 + (int32_t)tl, (int)(key - tl * nm), vals[q]);
+            keys[q] = UPD_EMPTY;
+            vals[q] = 0ull;
         }
-        __syncthreads();
-        if (tid == 0) n_touched = 0;
         __syncthreads();
     }
-    double *part = WRITE ? u.part_sq : u.part_norm;
-    const int64_t ob = ((int64_t)tile * u.n_chunks + c) * u.m_tile;
-    for (int m = tid; m < mt; m += UPD_THREADS) part[ob + m] = nrm[m];
 }
 
-static size_t update_smem(int m_tile) { return (size_t)m_tile * 20; }
+template <bool WRITE>
+__global__ void __launch_bounds__(UPD_HEAVY_THREADS) k_upd_heavy(UpdateArgs u) {
+    extern __shared__ unsigned long long acc[];                              // [UPD_TILE]
+    int32_t *touched = reinterpret_cast<int32_t *>(acc + UPD_TILE);          // [UPD_TILE]
+    __shared__ int32_t n_touched;
+    for (int q = threadIdx.x; q < UPD_TILE; q += UPD_HEAVY_THREADS) acc[q] = 0ull;
+    if (threadIdx.x == 0) n_touched = 0;
+    __syncthreads();
+    for (int h = blockIdx.x; h < u.n_heavy; h += gridDim.x) {
+        const int32_t t = u.heavy_terms[h];
+        const int64_t pb = u.col_ptr[t], pe = u.col_ptr[t + 1];
+        for (int m0 = 0; m0 < u.n_moved; m0 += UPD_TILE) {
+            const int mt = min(UPD_TILE, u.n_moved - m0);
+            for (int64_t p = pb + threadIdx.x; p < pe; p += UPD_HEAVY_THREADS) {
+                const int mm = __ldg(u.mdoc + __ldg(u.row_idx + p)) - m0;
+                if (mm < 0 || mm >= mt) continue;
+                const unsigned long long q = fixed_point(__ldg(u.cval + p), u.F);
+                if (q != 0ull && atomicAdd(acc + mm, q) == 0ull) touched[atomicAdd(&n_touched, 1)] = mm;
+            }
+            __syncthreads();
+            const int nt = n_touched;
+            for (int e = threadIdx.x; e < nt; e += UPD_HEAVY_THREADS) {
+                const int mm = touched[e];
+                const unsigned long long S = acc[mm];
+                acc[mm] = 0ull;
+                update_entry<WRITE>(u, t, m0 + mm, S);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) n_touched = 0;
+            __syncthreads();
+        }
+    }
+}
 
 static cudaError_t launch_update(const UpdateArgs &u, bool write, cudaStream_t st) {
-    if (u.n_chunks <= 0 || u.n_moved <= 0) return cudaSuccess;
-    const int tiles = (u.n_moved + u.m_tile - 1) / u.m_tile;
-    const size_t smem = update_smem(u.m_tile);
-    dim3 grid(u.n_chunks, tiles);
+    if (u.n_moved <= 0) return cudaSuccess;
     cudaError_t e;
-    if (write) {
-        e = cudaFuncSetAttribute(k_update<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem_l = (size_t)UPD_SLOTS * (sizeof(unsigned long long) + sizeof(uint32_t));
+    const size_t smem_h = (size_t)UPD_TILE * (sizeof(unsigned long long) + sizeof(int32_t));
+    if (u.n_light > 0) {
+        const int grid = min(u.n_light, 152 * 2 * 8);
+        if (write) {
+            e = cudaFuncSetAttribute(k_upd_light<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_l);
+            if (e != cudaSuccess) return e;
+            k_upd_light<true><<<grid, UPD_LIGHT_THREADS, smem_l, st>>>(u);
+        } else {
+            e = cudaFuncSetAttribute(k_upd_light<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_l);
+            if (e != cudaSuccess) return e;
+            k_upd_light<false><<<grid, UPD_LIGHT_THREADS, smem_l, st>>>(u);
+        }
+        e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        k_update<true><<<grid, UPD_THREADS, smem, st>>>(u);
-    } else {
-        e = cudaFuncSetAttribute(k_update<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_update<false><<<grid, UPD_THREADS, smem, st>>>(u);
     }
+    if (u.n_heavy > 0) {
+        const int grid = min(u.n_heavy, 152 * 4);
+        if (write) {
+            e = cudaFuncSetAttribute(k_upd_heavy<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_h);
+            if (e != cudaSuccess) return e;
+            k_upd_heavy<true><<<grid, UPD_HEAVY_THREADS, smem_h, st>>>(u);
+        } else {
+            e = cudaFuncSetAttribute(k_upd_heavy<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_h);
+            if (e != cudaSuccess) return e;
+            k_upd_heavy<false><<<grid, UPD_HEAVY_THREADS, smem_h, st>>>(u);
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_update_norm(const UpdateArgs &u, cudaStream_t st) { return launch_update(u, false, st); }
+cudaError_t launch_update_write(const UpdateArgs &u, cudaStream_t st) { return launch_update(u, true, st); }
+int update_chunk_postings() { return UPD_CHUNK; }
+
+// normsq[m] = ||S_m||^2 and inv_norm[m] = 1 / ||S_m|| from the 128-bit fixed-point sums
+// (units 2^-2F); newsq[m] from the 128-bit sums of c^2 (units 2^-62).
+__global__ void k_from_u128(const unsigned long long *normsq128, const unsigned long long *sq128, int32_t n,
+                            int F, double *normsq, double *inv_norm, double *newsq) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    if (normsq128) {
+        const double v = ldexp((double)normsq128[2 * m + 1], 64 - 2 * F) + ldexp((double)normsq128[2 * m], -2 * F);
+        normsq[m] = v;
+        inv_norm[m] = v > 0.0 ? 1.0 / sqrt(v) : 0.0;
+    }
+    if (sq128) newsq[m] = ldexp((double)sq128[2 * m + 1], 2) + ldexp((double)sq128[2 * m], -62);
+}
+
+cudaError_t launch_from_u128(const unsigned long long *normsq128, const unsigned long long *sq128, int32_t n,
+                             int F, double *normsq, double *inv_norm, double *newsq, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_from_u128<<<(n + 255) / 256, 256, 0, st>>>(normsq128, sq128, n, F, normsq, inv_norm, newsq);
     return cudaGetLastError();
 }
-
-cudaError_t launch_update_norm(const UpdateArgs &u, cudaStream_t st) {
-    return launch_update(u, false, st);
-}
-cudaError_t launch_update_write(const UpdateArgs &u, cudaStream_t st) {
-    return launch_update(u, true, st);
-}
-
-int update_tile() { return UPD_TILE; }
 
 // ------------------------------------------------------------------------------------
 // Moved columns before the write pass: a recomputed cluster's column is zeroed in the FP32
@@ -443,37 +531,6 @@ cudaError_t launch_mdoc(const int32_t *a, const int32_t *pos_in_m, int64_t n, in
     return cudaGetLastError();
 }
 
-
-// Column sums over chunks, chunk order (deterministic).
-__global__ void k_reduce_parts(const double *part, int32_t n_chunks, int32_t m_tile,
-                               int32_t n_moved, double *out) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= n_moved) return;
-    const int tile = m / m_tile, mm = m % m_tile;
-    const double *p = part + (int64_t)tile * n_chunks * m_tile + mm;
-    double s = 0.0;
-    for (int c = 0; c < n_chunks; ++c) s += p[(int64_t)c * m_tile];
-    out[m] = s;
-}
-
-cudaError_t launch_reduce_parts(const double *part, int32_t n_chunks, int32_t m_tile,
-                                int32_t n_moved, double *out, cudaStream_t st) {
-    if (n_moved <= 0) return cudaSuccess;
-    k_reduce_parts<<<(n_moved + 255) / 256, 256, 0, st>>>(part, n_chunks, m_tile, n_moved, out);
-    return cudaGetLastError();
-}
-
-__global__ void k_inv_norm(const double *normsq, int32_t n, double *inv) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m < n) inv[m] = normsq[m] > 0.0 ? 1.0 / sqrt(normsq[m]) : 0.0;
-}
-
-cudaError_t launch_inv_norm(const double *normsq, int32_t n_moved, double *inv_norm,
-                            cudaStream_t st) {
-    if (n_moved <= 0) return cudaSuccess;
-    k_inv_norm<<<(n_moved + 255) / 256, 256, 0, st>>>(normsq, n_moved, inv_norm);
-    return cudaGetLastError();
-}
 
 // ------------------------------------------------------------------------------------
 // Objective terms: one warp per document of a moved cluster, FP64 dot x_i . c_{a_i}(old)
