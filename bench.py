@@ -155,10 +155,17 @@ def oracle_sample_rate(docs, C32: np.ndarray, seed: int, budget_s: float = 15.0)
     sample of the workload's documents: returns (docs/s, sample size, seconds, threads)."""
     import oracle
     from paper_2108_00895_gb300 import synth
-    probe = docs.rows(synth.sample_ids(docs.n_docs, 64, seed))
-    t0 = time.perf_counter()
-    oracle.assign(probe, C32)
-    per_doc = max((time.perf_counter() - t0) / probe.n_docs, 1e-7)
+    # calibrate on growing probes until one takes at least 0.5 s, then size the sample
+    n_probe, per_doc = 64, None
+    while True:
+        probe = docs.rows(synth.sample_ids(docs.n_docs, n_probe, seed))
+        t0 = time.perf_counter()
+        oracle.assign(probe, C32)
+        dt = time.perf_counter() - t0
+        per_doc = max(dt / probe.n_docs, 1e-8)
+        if dt >= 0.5 or n_probe >= docs.n_docs:
+            break
+        n_probe = min(docs.n_docs, n_probe * 4)
     n = int(min(docs.n_docs, max(64, budget_s / per_doc)))
     sample = docs.rows(synth.sample_ids(docs.n_docs, n, seed + 1))
     t0 = time.perf_counter()
@@ -181,10 +188,16 @@ def run_reference(args, w, world, rank, dist):
         a, b = docs.row_ptr[i], docs.row_ptr[i + 1]
         C0[docs.col_idx[a:b], j] = docs.values[a:b]
     # size one step's sample so that warmup + steps stay within a few minutes
-    probe = docs.rows(synth.sample_ids(docs.n_docs, 32, 7))
-    t0 = time.perf_counter()
-    oracle.assign(probe, C0)
-    per_doc = max((time.perf_counter() - t0) / probe.n_docs, 1e-7)
+    n_probe = 32
+    while True:
+        probe = docs.rows(synth.sample_ids(docs.n_docs, n_probe, 7))
+        t0 = time.perf_counter()
+        oracle.assign(probe, C0)
+        dt = time.perf_counter() - t0
+        per_doc = max(dt / probe.n_docs, 1e-8)
+        if dt >= 0.5 or n_probe >= docs.n_docs:
+            break
+        n_probe = min(docs.n_docs, n_probe * 4)
     total_budget = 150.0
     n = int(min(docs.n_docs, max(32, total_budget / (args.steps + args.warmup) / per_doc)))
     times = []
@@ -333,9 +346,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--profile-run", action="store_true",
+                    help="allow fewer warm-up steps (launch lists under a profiler; not a timed number)")
     args = ap.parse_args()
-    if args.warmup < 3:
-        ap.error("--warmup must be >= 3")
+    if args.warmup < 3 and not args.profile_run:
+        ap.error("--warmup must be >= 3 (timed numbers need three warm-up steps)")
     from paper_2108_00895_gb300 import workloads
     w = workloads.ALL[args.workload]
     world, rank, local, dist = dist_setup(args)
