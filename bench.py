@@ -335,13 +335,89 @@ def run_ours(args, w, world, rank, local, dist):
         print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ batched form
+def run_batched(args, world, rank, local, dist):
+    """Batched form: all instances of the batched workload in one skm_fit_batched call per step
+    (persistent scoring launch over all instances, loop captured in a CUDA graph)."""
+    import tempfile
+
+    import torch
+
+    from paper_2108_00895_gb300 import skm, workloads
+    W = workloads.BATCHED
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    skm.load()
+    inst = W.instances()
+    n_total = sum(d.n_docs for d, _, _ in inst)
+    dinst = [((torch.from_numpy(d.row_ptr).to(dev), torch.from_numpy(d.col_idx).to(dev),
+               torch.from_numpy(d.values).to(dev), d.n_terms), k, ids) for d, k, ids in inst]
+    cache = os.path.join(tempfile.gettempdir(), f"skm_tune_{os.getpid()}.txt")
+    for _ in range(args.warmup):
+        skm.fit_batched(dinst, W.max_iter, tau=args.tau, use_graph=True, tune_cache=cache, device=local)
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(dist)
+    t0 = time.perf_counter()
+    loop_ms, fmas, st = 0.0, 0, None
+    for _ in range(args.steps):
+        _, st = skm.fit_batched(dinst, W.max_iter, tau=args.tau, use_graph=True, tune_cache=cache, device=local)
+        loop_ms += st["ms_loop"]
+        fmas += st["fmas"]
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    barrier(dist)
+    clk = clocks.stop()
+    t_max = max_over_ranks(dist, dt, dev)
+    docs_done = sum_over_ranks(dist, float(n_total * W.max_iter * args.steps), dev)
+    e2e = None
+    if not args.no_e2e:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            skm.fit_batched(inst, W.max_iter, tau=args.tau, use_graph=True, tune_cache=cache, device=local)
+        e_dt = max_over_ranks(dist, time.perf_counter() - t0, dev)
+        e2e = {"value": docs_done / e_dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(sum(8 * (d.n_docs + 1) + 8 * d.nnz for d, _, _ in inst)),
+               "d2h_bytes_per_step": int(4 * n_total + 8 * W.max_iter * len(inst))}
+    pk = peaks()
+    ach = 2.0 * fmas / (loop_ms / 1e3) / 1e12 if loop_ms > 0 else None
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        docs0, k0, ids0 = max(inst, key=lambda x: x[0].nnz * x[1])
+        C0 = np.zeros((docs0.n_terms, k0), np.float32)
+        for j, i in enumerate(ids0):
+            a, b = docs0.row_ptr[i], docs0.row_ptr[i + 1]
+            C0[docs0.col_idx[a:b], j] = docs0.values[a:b]
+        rate, n, cdt, cores = oracle_sample_rate(docs0, C0, 4243, args.cpu_budget)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{n} documents of the largest instance (k={k0}), one assignment step against its "
+                         f"initial centroids, {cdt:.1f} s"}
+    if os.path.exists(cache):
+        os.remove(cache)
+    if rank == 0:
+        line = {"metric": METRIC, "value": docs_done / t_max, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": dict(W.describe(), step="one skm_fit_batched call over all instances (setup + loop)",
+                               docs_total=n_total, parallelism=f"replicas x{world}",
+                               l2="inputs larger than L2", graph_nodes=st["graph_nodes"] if st else None,
+                               shapes=st["shape_instances"] if st else None),
+                "roofline": {"bound": "alu", "achieved": ach, "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
+                             "frac": ach / pk["fp32_tflops"] if ach else None, "traffic": None,
+                             "kernel": "whole iteration loop (all kernels; a lower bound for the scoring kernel)",
+                             "loop_ms_per_step": loop_ms / args.steps},
+                "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": None}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["large", "medium", "small"], default="large")
+    ap.add_argument("--workload", choices=["large", "medium", "small", "batched"], default="large")
     ap.add_argument("--tau", type=float, default=1e-4)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -352,8 +428,39 @@ def main():
     if args.warmup < 3 and not args.profile_run:
         ap.error("--warmup must be >= 3 (timed numbers need three warm-up steps)")
     from paper_2108_00895_gb300 import workloads
-    w = workloads.ALL[args.workload]
     world, rank, local, dist = dist_setup(args)
+    if args.workload == "batched":
+        try:
+            if args.impl == "reference":
+                if rank == 0:
+                    W = workloads.BATCHED
+                    inst = W.instances()
+                    docs0, k0, ids0 = max(inst, key=lambda x: x[0].nnz * x[1])
+                    C0 = np.zeros((docs0.n_terms, k0), np.float32)
+                    for j, i in enumerate(ids0):
+                        a, b = docs0.row_ptr[i], docs0.row_ptr[i + 1]
+                        C0[docs0.col_idx[a:b], j] = docs0.values[a:b]
+                    times = []
+                    for s_ in range(args.warmup + args.steps):
+                        rate, n, cdt, cores = oracle_sample_rate(docs0, C0, 100 + s_, 150.0 / (args.warmup + args.steps))
+                        if s_ >= args.warmup:
+                            times.append(rate)
+                    value = float(np.mean(times))
+                    print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+                                      "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                                      "dtype": "f64", "data": "synthetic", "config": W.describe(),
+                                      "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                                       "sample": f"{n} documents of the largest instance per step"},
+                                      "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                              "d2h_bytes_per_step": 0}}), flush=True)
+            else:
+                run_batched(args, world, rank, local, dist)
+        finally:
+            if dist is not None:
+                dist.destroy_process_group()
+        return
+    w = workloads.ALL[args.workload]
     try:
         if args.impl == "reference":
             run_reference(args, w, world, rank, dist)

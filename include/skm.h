@@ -175,6 +175,54 @@ SKM_API skm_status skm_get_stats(const skm_ctx *ctx, skm_stats *out);
 /* Device bytes currently held by the context. */
 SKM_API size_t skm_mem_used(const skm_ctx *ctx);
 
+/* ------------------------------------------------------------------------------------
+ * Batched form: many independent clustering instances of different sizes in one call.
+ * Each instance runs the plain Lloyd loop of Sec. 2 (assignment against all k FP32
+ * centroids with FP64 rescoring of near ties, then the update of the clusters whose
+ * membership changed) for exactly max_iter assignment steps; an instance that converges
+ * earlier keeps its assignment and centroids. All instances advance together: every phase of
+ * an iteration is one launch over all of them (the scoring pass is a persistent kernel over
+ * one queue of tiles), and the loop is captured once in a CUDA graph when use_graph = 1.
+ * ---------------------------------------------------------------------------------- */
+typedef struct {
+    skm_csr docs;                 /* the instance's documents, host or device */
+    int32_t k;                    /* clusters, 1 <= k <= min(n_docs, 2048) */
+    const int32_t *init_doc_ids;  /* host int32[k], distinct: c_j = x_{init_doc_ids[j]} */
+    int32_t *assign_out;          /* int32[n_docs], host or device (as docs.on_device) */
+    double *objective_out;        /* host double[max_iter], nullable: objective of each step */
+} skm_batch_item;
+
+typedef struct {
+    int32_t max_iter;             /* assignment steps of every instance, >= 1 */
+    int32_t rescore;              /* 1: FP64 rescoring of near ties (exact argmax) */
+    double rescore_tau;           /* minimum margin threshold (raised to the error bound) */
+    int32_t device;
+    void *stream;                 /* cudaStream_t; NULL = legacy default stream */
+    skm_alloc_fn alloc;           /* NULL: cudaMalloc / cudaFree; all memory is freed on return */
+    skm_free_fn free;
+    void *alloc_user;
+    const char *tune_cache;       /* autotuner cache file (read and updated), NULL = none */
+    int32_t use_graph;            /* 1: capture the iteration loop in a CUDA graph */
+} skm_batch_config;
+
+typedef struct {
+    double ms_total;              /* wall time of the call */
+    double ms_setup;              /* validation, transposes, autotuning, tables */
+    double ms_loop;               /* device time of the iteration loop (CUDA events) */
+    int64_t fmas;                 /* algorithmic multiply-adds of all scoring passes */
+    int64_t tiles;                /* scoring tiles per iteration */
+    int64_t graph_nodes;          /* nodes of the captured graph (0 without a graph) */
+    int64_t device_bytes;         /* device memory used */
+    int32_t tuned;                /* instances timed by the autotuner (cache misses) */
+    int32_t shape_instances[5];   /* instances per scoring shape: lane16, lane32, 128, 256, 512 */
+    char message[256];            /* reason of a failure, "" on success */
+} skm_batch_stats;
+
+/* Runs every item to max_iter assignment steps. Synchronous. stats is nullable. Errors:
+ * SKM_ERR_INVALID (bad config or item), SKM_ERR_OOM, SKM_ERR_CUDA; stats->message says why. */
+SKM_API skm_status skm_fit_batched(const skm_batch_config *cfg, const skm_batch_item *items, int32_t n_items,
+                                   skm_batch_stats *stats);
+
 /*
  * Assignment step that allocates no device memory. The paper has no counterpart: this is a
  * service of the library for callers that cannot let a library allocate -- callers whose

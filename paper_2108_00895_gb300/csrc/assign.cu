@@ -7,30 +7,11 @@
 // score is a pure function of (x_i, c_j): the pruned and the full pass agree bit for bit.
 #include <cstdlib>
 
+#include "skm_device.cuh"
 #include "skm_internal.cuh"
 #include "skm_kernels.cuh"
 
 namespace skm {
-
-// acc[q] += v * (two consecutive columns of the loaded row segment), one paired FP32
-// fused multiply-add per two columns; each half rounds exactly like a scalar fmaf.
-template <typename CT, int NV>
-__device__ __forceinline__ void fma_row(float2 (&acc)[NV * 16 / (int)sizeof(CT) / 2], float v,
-                                        const uint4 (&w)[NV]) {
-    const float2 vv = make_float2(v, v);
-#pragma unroll
-    for (int u = 0; u < NV; ++u) {
-        const uint32_t ww[4] = {w[u].x, w[u].y, w[u].z, w[u].w};
-        if constexpr (sizeof(CT) == 4) {
-            acc[u * 2 + 0] = __ffma2_rn(vv, make_float2(__uint_as_float(ww[0]), __uint_as_float(ww[1])), acc[u * 2 + 0]);
-            acc[u * 2 + 1] = __ffma2_rn(vv, make_float2(__uint_as_float(ww[2]), __uint_as_float(ww[3])), acc[u * 2 + 1]);
-        } else {
-#pragma unroll
-            for (int h = 0; h < 4; ++h)
-                acc[u * 4 + h] = __ffma2_rn(vv, make_float2(bf16lo(ww[h]), bf16hi(ww[h])), acc[u * 4 + h]);
-        }
-    }
-}
 
 // ------------------------------------------------------------------------------------
 // k_score: one warp per (document, slice). Lane l owns, for u in [0, NV), the EPV columns
@@ -43,7 +24,6 @@ __global__ void __launch_bounds__(256) k_score(ScoreArgs a) {
     constexpr int EPV = 16 / (int)sizeof(CT);   // elements per 16-byte vector
     constexpr int J = NV * EPV;                  // columns per lane
     constexpr int KS = 32 * J;                   // columns per slice
-    constexpr int G = NV >= 4 ? 2 : 4;           // nonzeros whose rows are loaded together
     __shared__ int2 stage[8][32];                // per warp: 32 (t, x) pairs
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -51,88 +31,16 @@ __global__ void __launch_bounds__(256) k_score(ScoreArgs a) {
     if (pos >= a.n_list) return;
     const int slice = blockIdx.y;
     const int64_t i = a.doc_list ? (int64_t)a.doc_list[pos] : (int64_t)pos;
-    const int64_t beg = a.row_ptr[i], end = a.row_ptr[i + 1];
     const int64_t j0 = (int64_t)slice * KS;
-    const CT *Cs = reinterpret_cast<const CT *>(a.C) + j0 + lane * EPV;
-
     float2 acc[J / 2];
-#pragma unroll
-    for (int q = 0; q < J / 2; ++q) acc[q] = make_float2(0.f, 0.f);
-
-    for (int64_t b = beg; b < end; b += 32) {
-        const int n = (int)min((int64_t)32, end - b);
-        __syncwarp();
-        if (lane < n) stage[wib][lane] = make_int2(__ldg(a.col + b + lane), __float_as_int(__ldg(a.val + b + lane)));
-        __syncwarp();
-        int q = 0;
-        for (; q + G <= n; q += G) {
-            uint4 w[G][NV];
-            float v[G];
-#pragma unroll
-            for (int g = 0; g < G; ++g) {
-                const int2 tv = stage[wib][q + g];
-                v[g] = __int_as_float(tv.y);
-                const CT *row = Cs + (int64_t)tv.x * a.ldc;
-#pragma unroll
-                for (int u = 0; u < NV; ++u) w[g][u] = ldg16(row + u * 32 * EPV);
-            }
-#pragma unroll
-            for (int g = 0; g < G; ++g) fma_row<CT, NV>(acc, v[g], w[g]);
-        }
-        for (; q < n; ++q) {
-            const int2 tv = stage[wib][q];
-            const CT *row = Cs + (int64_t)tv.x * a.ldc;
-            uint4 w[NV];
-#pragma unroll
-            for (int u = 0; u < NV; ++u) w[u] = ldg16(row + u * 32 * EPV);
-            fma_row<CT, NV>(acc, __int_as_float(tv.y), w);
-        }
-    }
-
+    slice_accumulate<CT, NV>(a.row_ptr[i], a.row_ptr[i + 1], a.col, a.val,
+                             reinterpret_cast<const CT *>(a.C) + j0 + lane * EPV, a.ldc, stage[wib], lane, acc);
     if constexpr (COLLECT) {
-        // same scores as the top-list pass; append every one at or above the threshold
-        const float thr = a.thr[pos];
-#pragma unroll
-        for (int u = 0; u < NV; ++u) {
-#pragma unroll
-            for (int e = 0; e < EPV; ++e) {
-                const int64_t c = j0 + u * 32 * EPV + lane * EPV + e;
-                const int qq = (u * EPV + e) >> 1;
-                const float sc = (e & 1) ? acc[qq].y : acc[qq].x;
-                if (c < a.ncols && sc >= thr) {
-                    const int id = a.col_ids ? __ldg(a.col_ids + c) : (int)c;
-                    const int at = atomicAdd(a.cand_cnt + pos, 1);
-                    if (at < a.cap) a.cand[(int64_t)pos * a.cap + at] = id;
-                }
-            }
-        }
+        slice_collect<CT, NV>(acc, j0, lane, a.ncols, a.col_ids, a.thr[pos], a.cand_cnt + pos,
+                              a.cand + (int64_t)pos * a.cap, a.cap);
     } else {
-        float ls[TOPT];
-        int lj[TOPT];
-#pragma unroll
-        for (int q = 0; q < TOPT; ++q) { ls[q] = -INFINITY; lj[q] = INT32_MAX; }
-#pragma unroll
-        for (int u = 0; u < NV; ++u) {
-#pragma unroll
-            for (int e = 0; e < EPV; ++e) {
-                const int64_t c = j0 + u * 32 * EPV + lane * EPV + e;
-                if (c < a.ncols) {
-                    const int id = a.col_ids ? __ldg(a.col_ids + c) : (int)c;
-                    const int qq = (u * EPV + e) >> 1;
-                    topt_insert(ls, lj, (e & 1) ? acc[qq].y : acc[qq].x, id);
-                }
-            }
-        }
-        topt_warp_merge(ls, lj);
-        if (lane < TOPT) {
-            float s = ls[0];
-            int j = lj[0];
-#pragma unroll
-            for (int q = 1; q < TOPT; ++q) if (lane == q) { s = ls[q]; j = lj[q]; }
-            const int64_t o = ((int64_t)slice * a.n_list + pos) * TOPT + lane;
-            a.part_s[o] = s;
-            a.part_j[o] = j;
-        }
+        slice_topt_write<CT, NV>(acc, j0, lane, a.ncols, a.col_ids, a.part_s, a.part_j,
+                                 ((int64_t)slice * a.n_list + pos) * TOPT);
     }
 }
 
@@ -182,21 +90,6 @@ cudaError_t launch_score(const ScoreArgs &a, int precision, int slice_cols, cuda
 // document's threshold.
 cudaError_t launch_collect(const ScoreArgs &a, int precision, int slice_cols, cudaStream_t st) {
     return launch_score_t<true>(a, precision, slice_cols, st);
-}
-
-// ------------------------------------------------------------------------------------
-// Error bound of the scoring pass for one document (all data are non-negative):
-//   |s_hat - s| <= beta * s,  beta = u_c + gamma_n * (1 + u_c),
-// u_c the unit roundoff of the centroid copy (2^-9 for BF16 round-to-nearest-even, 0 for
-// the FP32 master itself) and gamma_n = n u / (1 - n u), u = 2^-24, n = nonzeros of the
-// document (one rounding per fused multiply-add).
-// ------------------------------------------------------------------------------------
-__device__ __forceinline__ double score_beta(int precision, int64_t nnz) {
-    const double u = 5.9604644775390625e-08;  // 2^-24
-    const double nu = (double)nnz * u;
-    const double gam = nu / (1.0 - nu);
-    const double uc = precision == 1 ? 1.953125e-03 : 0.0;  // 2^-9
-    return uc + gam * (1.0 + uc);
 }
 
 // ------------------------------------------------------------------------------------

@@ -16,6 +16,7 @@
 // accumulates the squared norm of the stored FP32 column (for the next step's shift). The objective term
 // S_j . c_j(old) comes from per-document FP64 dots against the old master (k_doc_obj),
 // summed per cluster in fixed point, before the update overwrites it.
+#include "skm_device.cuh"
 #include "skm_kernels.cuh"
 
 namespace skm {
@@ -301,26 +302,6 @@ constexpr uint32_t UPD_EMPTY = 0xffffffffu;
 constexpr int UPD_LIGHT_THREADS = 512;
 constexpr int UPD_HEAVY_THREADS = 1024;
 constexpr int UPD_TILE = 16384;               // moved entries per heavy-term tile (12 bytes each)
-
-// round(x * 2^F) for a finite x >= 0 from its bits (integer arithmetic only; ties round up)
-__device__ __forceinline__ unsigned long long fixed_point(float x, int F) {
-    const uint32_t b = __float_as_uint(x);
-    const int e = (int)(b >> 23);
-    if (e == 0 && (b & 0x7fffffu) == 0) return 0ull;
-    const unsigned long long mant = (unsigned long long)((b & 0x7fffffu) | (e ? 0x800000u : 0u));
-    const int sh = (e ? e : 1) - 150 + F;      // x = mant * 2^((e ? e : 1) - 150)
-    if (sh >= 0) return mant << sh;
-    if (sh <= -25) return 0ull;
-    return (mant + (1ull << (-sh - 1))) >> (-sh);
-}
-
-// acc (two 64-bit words, low first) += x (hi:lo); order-independent exact 128-bit sum
-__device__ __forceinline__ void atomic_add_u128(unsigned long long *acc, unsigned long long lo,
-                                                unsigned long long hi) {
-    const unsigned long long old = atomicAdd(acc, lo);
-    hi += (old + lo < old) ? 1ull : 0ull;
-    if (hi) atomicAdd(acc + 1, hi);
-}
 
 // S (fixed point, 2^-F units) of entry m of term t: the norm or write step.
 template <bool WRITE>

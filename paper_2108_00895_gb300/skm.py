@@ -62,9 +62,34 @@ class skm_stats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class skm_batch_item(ctypes.Structure):
+    _fields_ = [("docs", skm_csr), ("k", ctypes.c_int32), ("init_doc_ids", ctypes.c_void_p),
+                ("assign_out", ctypes.c_void_p), ("objective_out", ctypes.c_void_p)]
+
+
+class skm_batch_config(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int32), ("rescore", ctypes.c_int32), ("rescore_tau", ctypes.c_double),
+                ("device", ctypes.c_int32), ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN),
+                ("free", FREE_FN), ("alloc_user", ctypes.c_void_p), ("tune_cache", ctypes.c_char_p),
+                ("use_graph", ctypes.c_int32)]
+
+
+class skm_batch_stats(ctypes.Structure):
+    _fields_ = [("ms_total", ctypes.c_double), ("ms_setup", ctypes.c_double), ("ms_loop", ctypes.c_double),
+                ("fmas", ctypes.c_int64), ("tiles", ctypes.c_int64), ("graph_nodes", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("tuned", ctypes.c_int32),
+                ("shape_instances", ctypes.c_int32 * 5), ("message", ctypes.c_char * 256)]
+
+    def as_dict(self) -> dict:
+        d = {name: getattr(self, name) for name, _ in self._fields_ if name not in ("shape_instances", "message")}
+        d["shape_instances"] = dict(zip(("lane16", "lane32", "w128", "w256", "w512"), list(self.shape_instances)))
+        d["message"] = self.message.decode(errors="replace")
+        return d
+
+
 EXPORTS = ("skm_config_default", "skm_create", "skm_destroy", "skm_last_error", "skm_fit",
            "skm_assign", "skm_update", "skm_set_centroids", "skm_get_centroids", "skm_n_terms",
-           "skm_get_stats", "skm_mem_used", "skm_assign_fixed_scratch")
+           "skm_get_stats", "skm_mem_used", "skm_fit_batched", "skm_assign_fixed_scratch")
 
 # skm_assign_fixed_scratch: capacity of its fixed scratch, in (document x 256-column slice) units
 FIXED_SCRATCH_SLICE = 256
@@ -100,6 +125,8 @@ def load(build_if_missing: bool = True):
             "skm_mem_used": (ctypes.c_size_t, [P]),
             "skm_assign_fixed_scratch": (st, [ctypes.POINTER(skm_csr), ctypes.c_int32, P, ctypes.c_int64,
                                               P, P, P]),
+            "skm_fit_batched": (st, [ctypes.POINTER(skm_batch_config), ctypes.POINTER(skm_batch_item),
+                                     ctypes.c_int32, ctypes.POINTER(skm_batch_stats)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -217,6 +244,56 @@ def skm_assign_fixed_scratch(csr: skm_csr, k: int, centroids, ld: int, assign_ou
                                          _ptr(assign_out), _ptr(score_out), stream or None)
     if st != SKM_OK:
         raise SkmError(st, "skm_assign_fixed_scratch failed")
+
+
+def skm_fit_batched(cfg: skm_batch_config, items, stats: skm_batch_stats) -> None:
+    arr = (skm_batch_item * len(items))(*items)
+    st = load().skm_fit_batched(ctypes.byref(cfg), arr, len(items), ctypes.byref(stats))
+    if st != SKM_OK:
+        raise SkmError(st, stats.message.decode(errors="replace"))
+
+
+def fit_batched(instances, max_iter: int, rescore: bool = True, tau: float = 0.0, use_graph: bool = True,
+                tune_cache: str | None = None, device: int = 0, stream: int | None = None,
+                allocator: str = "torch"):
+    """Batched form: instances = [(docs, k, init_ids), ...] with docs a ``synth.Csr`` (host) or a
+    (row_ptr, col_idx, values, n_terms) tuple of device tensors. Returns
+    ([(assign, objective[max_iter]), ...], stats dict)."""
+    cfg = skm_batch_config()
+    cfg.max_iter = int(max_iter)
+    cfg.rescore = int(bool(rescore))
+    cfg.rescore_tau = float(tau)
+    cfg.device = int(device)
+    cfg.use_graph = int(bool(use_graph))
+    cfg.tune_cache = tune_cache.encode() if tune_cache else None
+    alloc = None
+    if allocator == "torch":
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(device).cuda_stream
+        alloc = _TorchAllocator(int(device), int(stream or 0))
+        cfg.alloc = alloc.alloc_cb
+        cfg.free = alloc.free_cb
+    cfg.stream = stream or None
+    keep, items, outs = [], [], []
+    for docs, k, ids in instances:
+        if isinstance(docs, tuple) and len(docs) == 4:
+            csr, kp, on_dev = make_csr(docs[:3], docs[3])
+        else:
+            csr, kp, on_dev = make_csr(docs)
+        ids = np.ascontiguousarray(ids, dtype=np.int32)
+        if on_dev:
+            import torch
+            a = torch.empty(csr.n_docs, dtype=torch.int32, device=kp[0].device)
+        else:
+            a = np.empty(csr.n_docs, np.int32)
+        obj = np.zeros(max_iter, np.float64)
+        keep.append((kp, ids, a, obj))
+        items.append(skm_batch_item(csr, int(k), _ptr(ids), _ptr(a), _ptr(obj)))
+        outs.append((a, obj))
+    stats = skm_batch_stats()
+    skm_fit_batched(cfg, items, stats)
+    return outs, stats.as_dict()
 
 
 def skm_get_stats(ctx) -> skm_stats:

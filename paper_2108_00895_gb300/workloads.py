@@ -68,3 +68,54 @@ LARGE = Workload("ncc-bf16 N=2000000 d=250000 k=10000", 2_000_000, 250_000, 10_0
                  1.05, 30, "bf16", "ncc", True, 3)
 
 ALL = {"small": SMALL, "medium": MEDIUM, "large": LARGE}
+
+
+@dataclass(frozen=True)
+class BatchedWorkload:
+    """Many independent clustering instances of different sizes (the batched form): per
+    instance N log-uniform in [n_lo, n_hi], d uniform over `vocab`, k log-uniform in
+    [k_lo, k_hi] (and at most N), lognormal(nnz_mean) lengths clipped to [5, 2000], Zipf terms,
+    FP32 centroids, a fixed number of Lloyd steps."""
+    name: str
+    n_instances: int
+    n_lo: int
+    n_hi: int
+    vocab: tuple
+    k_lo: int
+    k_hi: int
+    nnz_mean: float
+    zipf_s: float
+    max_iter: int
+    seed: int
+
+    def specs(self):
+        import math
+        u = synth.uniform(self.seed, 1, 3 * self.n_instances)
+        out = []
+        for q in range(self.n_instances):
+            n = int(round(math.exp(math.log(self.n_lo) + u[3 * q] * (math.log(self.n_hi) - math.log(self.n_lo)))))
+            d = int(self.vocab[min(len(self.vocab) - 1, int(u[3 * q + 1] * len(self.vocab)))])
+            k = int(round(math.exp(math.log(self.k_lo) + u[3 * q + 2] * (math.log(self.k_hi) - math.log(self.k_lo)))))
+            out.append((n, d, min(k, n)))
+        return out
+
+    def instances(self):
+        """[(corpus, k, initial ids)] with seeds derived from the instance index."""
+        res = []
+        for q, (n, d, k) in enumerate(self.specs()):
+            docs = synth.make_corpus(n, d, self.nnz_mean, 5, 2000, self.zipf_s, self.seed * 1000 + q)
+            res.append((docs, k, synth.init_ids(n, k, self.seed * 1000 + 500 + q)))
+        return res
+
+    def describe(self) -> dict:
+        return {"workload": self.name, "instances": self.n_instances,
+                "n_docs": f"log-uniform [{self.n_lo}, {self.n_hi}]", "n_terms": list(self.vocab),
+                "k": f"log-uniform [{self.k_lo}, {self.k_hi}]",
+                "nnz": f"lognormal(mean {self.nnz_mean:g}) clipped to [5,2000]",
+                "terms": f"Zipf(s={self.zipf_s:g}) without replacement", "precision": "fp32",
+                "max_iter": self.max_iter, "seed": self.seed}
+
+
+# Batched form: 256 uneven instances, 20 Lloyd steps each, FP32.
+BATCHED = BatchedWorkload("batched-fp32 256 instances", 256, 1000, 200_000, (20_000, 50_000, 100_000), 16, 2048,
+                          80.0, 1.1, 20, 4)

@@ -1,0 +1,69 @@
+"""Batched form: uneven clustering instances in one call (persistent scoring launch, CUDA
+graph, autotuned shapes) must give each instance the oracle's result."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2108_00895_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+MARGIN = 1e-5
+OBJ_RTOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def skm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2108_00895_gb300 import skm as mod
+    mod.load()
+    return mod
+
+
+def _instances():
+    spec = [(900, 3000, 3), (2500, 6000, 16), (1300, 4000, 29), (4000, 8000, 100), (3100, 5000, 300),
+            (700, 2000, 12), (5000, 10000, 700)]
+    out = []
+    for q, (n, d, k) in enumerate(spec):
+        docs = synth.make_corpus(n, d, 40, 5, 300, 1.1, 3000 + q)
+        out.append((docs, k, synth.init_ids(n, k, 4000 + q)))
+    return out
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batched_instances_match_oracle(skm, tmp_path, use_graph):
+    inst = _instances()
+    max_iter = 8
+    cache = str(tmp_path / "tune.txt")
+    res, stats = skm.fit_batched(inst, max_iter, use_graph=use_graph, tune_cache=cache)
+    assert stats["message"] == ""
+    assert os.path.exists(cache) and stats["tuned"] > 0
+    if use_graph:
+        assert stats["graph_nodes"] > 0
+    assert sum(stats["shape_instances"].values()) == len(inst)
+    for (docs, k, ids), (a, obj) in zip(inst, res):
+        ref = oracle.fit(docs, k, ids, max_iter)
+        # the final assignment equals the oracle's (exact argmax; FP64 rescoring of near ties)
+        np.testing.assert_array_equal(a, ref.a)
+        t = ref.iters
+        np.testing.assert_allclose(obj[:t], ref.objective, rtol=OBJ_RTOL, atol=0)
+        # after convergence the assignment and objective stay fixed
+        if t < max_iter:
+            np.testing.assert_allclose(obj[t:], ref.objective[-1], rtol=OBJ_RTOL, atol=0)
+    # a second call reuses the cache and gives the same result
+    res2, stats2 = skm.fit_batched(inst, max_iter, use_graph=use_graph, tune_cache=cache)
+    assert stats2["tuned"] == 0
+    for (a, obj), (a2, obj2) in zip(res, res2):
+        np.testing.assert_array_equal(a, a2)
+        np.testing.assert_array_equal(obj, obj2)
+
+
+def test_batched_rejects_bad_items(skm):
+    docs = synth.make_corpus(100, 500, 10, 3, 30, 1.1, 77)
+    with pytest.raises(skm.SkmError) as e:
+        skm.fit_batched([(docs, 5, np.array([1, 1, 2, 3, 4]))], 3)
+    assert e.value.status == skm.SKM_ERR_INVALID
