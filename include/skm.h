@@ -223,6 +223,76 @@ typedef struct {
 SKM_API skm_status skm_fit_batched(const skm_batch_config *cfg, const skm_batch_item *items, int32_t n_items,
                                    skm_batch_stats *stats);
 
+/* ------------------------------------------------------------------------------------
+ * Serving form. A server answers assignment requests against a resident context (its
+ * centroids, set by skm_fit or skm_set_centroids, stay on the device) by continuous batching:
+ * every request waiting when the previous batch finishes joins the next batch (up to
+ * max_batch_docs documents and max_batch_nnz nonzeros), which runs as one assignment step.
+ * Clustering jobs run beside it on n_job_slots worker threads, each on a context and stream of
+ * its own, so batches and jobs overlap on the device. A job is started when its memory
+ * estimate fits the budget left by the resident context and the running jobs (the first
+ * waiting job that fits goes first); a job that could never fit is rejected at submission.
+ * Results do not depend on what else is running. Requests borrow the caller's host arrays:
+ * they must stay valid until skm_server_release. Thread-safe; the resident context must not be
+ * used by the caller while the server exists.
+ * ---------------------------------------------------------------------------------- */
+typedef struct skm_server skm_server;
+
+typedef struct {
+    int32_t device;
+    size_t mem_budget;            /* device bytes for the resident context and all jobs */
+    int32_t n_job_slots;          /* clustering jobs that may run at once (>= 0) */
+    int64_t max_batch_docs;       /* documents per assignment batch (and per request) */
+    int64_t max_batch_nnz;        /* nonzeros per assignment batch (a larger request runs alone) */
+    int32_t job_precision;        /* SKM_FP32 / SKM_BF16 for clustering jobs */
+    int32_t job_prune;            /* SKM_PRUNE_NONE / SKM_PRUNE_NCC for clustering jobs */
+    double rescore_tau;           /* rescoring threshold of clustering jobs */
+} skm_server_config;
+
+enum { SKM_REQ_QUEUED = 0, SKM_REQ_RUNNING = 1, SKM_REQ_DONE = 2, SKM_REQ_REJECTED = 3, SKM_REQ_FAILED = 4,
+       SKM_REQ_CANCELLED = 5 };
+
+typedef struct {
+    int32_t state;                /* SKM_REQ_* */
+    skm_status status;            /* of the finished request */
+    int64_t n_docs;
+    const int32_t *assign;        /* int32[n_docs], owned by the server until release */
+    const float *score;           /* assignment requests: similarity of the chosen centroid */
+    const double *objective;      /* clustering jobs: objective per assignment step */
+    int32_t iters;                /* clustering jobs: assignment steps run */
+    double latency_ms;            /* submission to completion */
+    double queue_ms;              /* submission to start */
+    int32_t batch_docs;           /* assignment requests: documents in the batch it ran in */
+    char message[256];
+} skm_server_result;
+
+typedef struct {
+    int64_t assign_submitted, assign_done, fit_submitted, fit_done, rejected, failed;
+    int64_t assign_batches, max_batch_docs_seen, docs_assigned, docs_clustered;
+    int64_t assign_queued, fit_queued;
+    int32_t jobs_running, peak_jobs_running;
+    size_t jobs_mem, resident_mem;
+} skm_server_stats;
+
+/* Start a server on a resident context. SKM_ERR_BUDGET if the resident context and a largest
+ * batch do not fit mem_budget. */
+SKM_API skm_status skm_server_create(const skm_server_config *cfg, skm_ctx *resident, skm_server **out);
+/* Queue an assignment request (host CSR with the resident vocabulary, at most max_batch_docs
+ * documents). Returns at once with a ticket. */
+SKM_API skm_status skm_server_submit_assign(skm_server *srv, const skm_csr *docs, uint64_t *ticket);
+/* Queue a clustering job: skm_fit of host CSR docs with k clusters from init_doc_ids (copied),
+ * max_iter assignment steps. Returns at once with a ticket. */
+SKM_API skm_status skm_server_submit_fit(skm_server *srv, const skm_csr *docs, int32_t k,
+                                         const int32_t *init_doc_ids, int32_t max_iter, uint64_t *ticket);
+/* Wait up to timeout_ms (< 0: no limit) for a request; SKM_ERR_TIMEOUT if it is not finished.
+ * The result's arrays stay valid until skm_server_release. */
+SKM_API skm_status skm_server_wait(skm_server *srv, uint64_t ticket, double timeout_ms, skm_server_result *res);
+/* Free a finished request's results. */
+SKM_API skm_status skm_server_release(skm_server *srv, uint64_t ticket);
+SKM_API skm_status skm_server_get_stats(skm_server *srv, skm_server_stats *out);
+/* Cancel waiting requests, let running ones finish, stop the workers and free the server. */
+SKM_API skm_status skm_server_destroy(skm_server *srv);
+
 /*
  * Assignment step that allocates no device memory. The paper has no counterpart: this is a
  * service of the library for callers that cannot let a library allocate -- callers whose

@@ -87,9 +87,38 @@ class skm_batch_stats(ctypes.Structure):
         return d
 
 
+class skm_server_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("mem_budget", ctypes.c_size_t), ("n_job_slots", ctypes.c_int32),
+                ("max_batch_docs", ctypes.c_int64), ("max_batch_nnz", ctypes.c_int64),
+                ("job_precision", ctypes.c_int32), ("job_prune", ctypes.c_int32), ("rescore_tau", ctypes.c_double)]
+
+
+class skm_server_result(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int), ("n_docs", ctypes.c_int64),
+                ("assign", ctypes.POINTER(ctypes.c_int32)), ("score", ctypes.POINTER(ctypes.c_float)),
+                ("objective", ctypes.POINTER(ctypes.c_double)), ("iters", ctypes.c_int32),
+                ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double), ("batch_docs", ctypes.c_int32),
+                ("message", ctypes.c_char * 256)]
+
+
+class skm_server_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("assign_submitted", "assign_done", "fit_submitted", "fit_done",
+                                              "rejected", "failed", "assign_batches", "max_batch_docs_seen",
+                                              "docs_assigned", "docs_clustered", "assign_queued", "fit_queued")] + \
+               [("jobs_running", ctypes.c_int32), ("peak_jobs_running", ctypes.c_int32),
+                ("jobs_mem", ctypes.c_size_t), ("resident_mem", ctypes.c_size_t)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+REQ_STATES = {0: "queued", 1: "running", 2: "done", 3: "rejected", 4: "failed", 5: "cancelled"}
+
 EXPORTS = ("skm_config_default", "skm_create", "skm_destroy", "skm_last_error", "skm_fit",
            "skm_assign", "skm_update", "skm_set_centroids", "skm_get_centroids", "skm_n_terms",
-           "skm_get_stats", "skm_mem_used", "skm_fit_batched", "skm_assign_fixed_scratch")
+           "skm_get_stats", "skm_mem_used", "skm_fit_batched", "skm_server_create", "skm_server_submit_assign",
+           "skm_server_submit_fit", "skm_server_wait", "skm_server_release", "skm_server_get_stats",
+           "skm_server_destroy", "skm_assign_fixed_scratch")
 
 # skm_assign_fixed_scratch: capacity of its fixed scratch, in (document x 256-column slice) units
 FIXED_SCRATCH_SLICE = 256
@@ -127,6 +156,14 @@ def load(build_if_missing: bool = True):
                                               P, P, P]),
             "skm_fit_batched": (st, [ctypes.POINTER(skm_batch_config), ctypes.POINTER(skm_batch_item),
                                      ctypes.c_int32, ctypes.POINTER(skm_batch_stats)]),
+            "skm_server_create": (st, [ctypes.POINTER(skm_server_config), P, ctypes.POINTER(P)]),
+            "skm_server_submit_assign": (st, [P, ctypes.POINTER(skm_csr), ctypes.POINTER(ctypes.c_uint64)]),
+            "skm_server_submit_fit": (st, [P, ctypes.POINTER(skm_csr), ctypes.c_int32, P, ctypes.c_int32,
+                                           ctypes.POINTER(ctypes.c_uint64)]),
+            "skm_server_wait": (st, [P, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(skm_server_result)]),
+            "skm_server_release": (st, [P, ctypes.c_uint64]),
+            "skm_server_get_stats": (st, [P, ctypes.POINTER(skm_server_stats)]),
+            "skm_server_destroy": (st, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -439,3 +476,92 @@ class SphericalKMeans:
 
     def mem_used(self) -> int:
         return int(self.lib.skm_mem_used(self.ctx))
+
+
+class Server:
+    """Serving form (see include/skm.h): continuous batching of assignment requests on a
+    resident context, clustering jobs beside it under a device-memory budget."""
+
+    def __init__(self, resident: "SphericalKMeans", mem_budget: int, n_job_slots: int = 2,
+                 max_batch_docs: int = 65536, max_batch_nnz: int = 65536 * 200, job_precision: str = "bf16",
+                 job_prune: str = "ncc", tau: float = 1e-4, device: int = 0):
+        self.lib = load()
+        cfg = skm_server_config()
+        cfg.device = int(device)
+        cfg.mem_budget = int(mem_budget)
+        cfg.n_job_slots = int(n_job_slots)
+        cfg.max_batch_docs = int(max_batch_docs)
+        cfg.max_batch_nnz = int(max_batch_nnz)
+        cfg.job_precision = {"fp32": SKM_FP32, "bf16": SKM_BF16}[job_precision]
+        cfg.job_prune = {"none": SKM_PRUNE_NONE, "ncc": SKM_PRUNE_NCC}[job_prune]
+        cfg.rescore_tau = float(tau)
+        self.resident = resident
+        h = ctypes.c_void_p()
+        st = self.lib.skm_server_create(ctypes.byref(cfg), resident.ctx, ctypes.byref(h))
+        if st != SKM_OK:
+            raise SkmError(st, "skm_server_create failed")
+        self.h = h
+        self._keep = {}
+
+    def submit_assign(self, docs) -> int:
+        csr, keep, on_dev = make_csr(docs)
+        t = ctypes.c_uint64(0)
+        st = self.lib.skm_server_submit_assign(self.h, ctypes.byref(csr), ctypes.byref(t))
+        if st != SKM_OK:
+            raise SkmError(st, "submit_assign rejected the request")
+        self._keep[t.value] = keep
+        return t.value
+
+    def submit_fit(self, docs, k: int, init_ids, max_iter: int) -> int:
+        csr, keep, on_dev = make_csr(docs)
+        ids = np.ascontiguousarray(init_ids, dtype=np.int32)
+        t = ctypes.c_uint64(0)
+        st = self.lib.skm_server_submit_fit(self.h, ctypes.byref(csr), int(k), _ptr(ids), int(max_iter),
+                                            ctypes.byref(t))
+        if st != SKM_OK:
+            raise SkmError(st, "submit_fit rejected the request")
+        self._keep[t.value] = keep
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: float = -1.0, release: bool = True) -> dict | None:
+        r = skm_server_result()
+        st = self.lib.skm_server_wait(self.h, ctypes.c_uint64(ticket), float(timeout_ms), ctypes.byref(r))
+        if st == SKM_ERR_TIMEOUT:
+            return None
+        if st != SKM_OK:
+            raise SkmError(st, "skm_server_wait failed")
+        n = int(r.n_docs)
+        out = {"state": REQ_STATES.get(r.state, r.state), "status": int(r.status), "n_docs": n,
+               "latency_ms": r.latency_ms, "queue_ms": r.queue_ms, "batch_docs": r.batch_docs,
+               "iters": r.iters, "message": r.message.decode(errors="replace")}
+        out["assign"] = np.ctypeslib.as_array(r.assign, shape=(n,)).copy() if r.assign else None
+        out["score"] = np.ctypeslib.as_array(r.score, shape=(n,)).copy() if r.score else None
+        out["objective"] = np.ctypeslib.as_array(r.objective, shape=(r.iters,)).copy() \
+            if r.objective and r.iters > 0 else None
+        if release:
+            self.lib.skm_server_release(self.h, ctypes.c_uint64(ticket))
+            self._keep.pop(ticket, None)
+        return out
+
+    def stats(self) -> dict:
+        s = skm_server_stats()
+        self.lib.skm_server_get_stats(self.h, ctypes.byref(s))
+        return s.as_dict()
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.skm_server_destroy(self.h)
+            self.h = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
