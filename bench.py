@@ -411,13 +411,126 @@ def run_batched(args, world, rank, local, dist):
         print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ serving form
+def run_serving(args, world, rank, local, dist):
+    """Serving form: open-loop Poisson arrivals against skm_server for a fixed window."""
+    import math
+
+    import torch
+
+    from paper_2108_00895_gb300 import skm, synth, workloads
+    W = workloads.SERVING
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    skm.load()
+    pool = W.pool()
+    # resident centroids: two Lloyd steps on the pool, loaded into an assignment-only context
+    with skm.SphericalKMeans(W.k, precision="bf16", prune="ncc", max_iter=2, allocator="cuda", device=local) as tmp:
+        tmp.fit(pool, synth.init_ids(pool.n_docs, W.k, 2000 + W.seed))
+        C = tmp.centroids()
+    stream = torch.cuda.Stream(dev)
+    resident = skm.SphericalKMeans(W.k, precision="bf16", rescore=True, tau=args.tau, allocator="cuda",
+                                   stream=stream.cuda_stream, device=local)
+    resident.set_centroids(C)
+    del C
+    budget = int(W.budget_gb * (1 << 30))
+    srv = skm.Server(resident, budget, n_job_slots=2, max_batch_docs=65536, max_batch_nnz=65536 * 300,
+                     job_precision="bf16", job_prune="ncc", tau=args.tau, device=local)
+    rng = np.random.default_rng(W.seed)
+    rp, col, val = pool.row_ptr, pool.col_idx, pool.values
+
+    def assign_req(n):
+        a = int(rng.integers(0, pool.n_docs - n))
+        return synth.Csr(rp[a:a + n + 1] - rp[a], col[rp[a]:rp[a + n]], val[rp[a]:rp[a + n]], pool.n_terms)
+
+    def job_req():
+        n = int(round(math.exp(rng.uniform(math.log(W.job_n_lo), math.log(W.job_n_hi)))))
+        k = int(round(math.exp(rng.uniform(math.log(W.job_k_lo), math.log(W.job_k_hi)))))
+        docs = synth.Csr(rp[:n + 1], col[:rp[n]], val[:rp[n]], pool.n_terms)   # prefix: zero copy
+        ids = np.unique(np.linspace(0, n - 1, k).astype(np.int32))
+        return docs, len(ids), ids
+
+    # warm-up: a few requests of each kind
+    for t in [srv.submit_assign(assign_req(64)) for _ in range(8)]:
+        srv.wait(t)
+    d0, k0, i0 = job_req()
+    srv.wait(srv.submit_fit(synth.Csr(rp[:10001], col[:rp[10000]], val[:rp[10000]], pool.n_terms), 64,
+                            np.arange(64, dtype=np.int32), 2))
+    window = args.serve_seconds
+    clocks = ClockSampler(local)
+    clocks.start()
+    tickets = []
+    t0 = time.perf_counter()
+    t_next = 0.0
+    while True:
+        t_next += rng.exponential(1.0 / W.rate)
+        if t_next > window:
+            break
+        now = time.perf_counter() - t0
+        if t_next > now:
+            time.sleep(t_next - now)
+        if rng.random() < W.p_assign:
+            n = int(round(math.exp(rng.uniform(0.0, math.log(W.assign_hi)))))
+            tickets.append(("assign", n, srv.submit_assign(assign_req(n))))
+        else:
+            docs, k, ids = job_req()
+            tickets.append(("fit", docs.n_docs, srv.submit_fit(docs, k, ids, W.job_iters)))
+    t_submit_end = time.perf_counter() - t0
+    lat_a, lat_f, docs_a, done_f, cl_docs, deferred, rejected = [], [], 0, 0, 0, 0, 0
+    for kind, n, t in tickets:   # assignments drain within a short grace period
+        if kind != "assign":
+            continue
+        res = srv.wait(t, timeout_ms=5000)
+        if res is not None and res["state"] == "done":
+            lat_a.append(res["latency_ms"])
+            docs_a += n
+    t_drain = time.perf_counter() - t0
+    stats = srv.stats()
+    for kind, n, t in tickets:
+        if kind != "fit":
+            continue
+        res = srv.wait(t, timeout_ms=0)
+        if res is None:
+            deferred += 1
+        elif res["state"] == "done":
+            done_f += 1
+            lat_f.append(res["latency_ms"])
+            cl_docs += n * res["iters"]
+        elif res["state"] == "rejected":
+            rejected += 1
+    clk = clocks.stop()
+    srv.close()
+    resident.close()
+    pct = lambda v, q: float(np.percentile(v, q)) if len(v) else None
+    n_assign = sum(1 for k_, _, _ in tickets if k_ == "assign")
+    n_fit = len(tickets) - n_assign
+    line = {"metric": "serving docs assigned/s; p50/p99 assignment latency (ms)", "value": docs_a / t_drain,
+            "unit": "docs/s", "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": 1e3 * t_drain,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": dict(W.describe(), window_s=window, job_slots=2, max_batch_docs=65536),
+            "serving": {"assign_requests": n_assign, "assign_done": len(lat_a),
+                        "assign_p50_ms": pct(lat_a, 50), "assign_p99_ms": pct(lat_a, 99),
+                        "assign_docs_per_s": docs_a / t_drain, "offered_assign_docs_per_s":
+                            sum(n for k_, n, _ in tickets if k_ == "assign") / window,
+                        "fit_requests": n_fit, "fit_done": done_f, "fit_deferred_at_end": deferred,
+                        "fit_rejected": rejected, "fit_p50_ms": pct(lat_f, 50), "fit_p99_ms": pct(lat_f, 99),
+                        "clustered_docs_per_s": cl_docs / t_drain, "assign_batches": stats["assign_batches"],
+                        "max_batch_docs": stats["max_batch_docs_seen"], "peak_jobs_running": stats["peak_jobs_running"],
+                        "submit_seconds": t_submit_end, "drain_seconds": t_drain},
+            "clocks": clk, "e2e": {"value": docs_a / t_drain, "unit": "docs/s",
+                                   "h2d_bytes_per_step": None, "d2h_bytes_per_step": None}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["large", "medium", "small", "batched"], default="large")
+    ap.add_argument("--workload", choices=["large", "medium", "small", "batched", "serving"], default="large")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving window (open loop)")
     ap.add_argument("--tau", type=float, default=1e-4)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -429,6 +542,17 @@ def main():
         ap.error("--warmup must be >= 3 (timed numbers need three warm-up steps)")
     from paper_2108_00895_gb300 import workloads
     world, rank, local, dist = dist_setup(args)
+    if args.workload == "serving":
+        try:
+            if args.impl == "reference":
+                print(json.dumps({"impl": "reference", "unavailable": "the serving form has no CPU counterpart; "
+                                  "the oracle arm is timed on the large workload"}))
+            else:
+                run_serving(args, world, rank, local, dist)
+        finally:
+            if dist is not None:
+                dist.destroy_process_group()
+        return
     if args.workload == "batched":
         try:
             if args.impl == "reference":

@@ -270,23 +270,28 @@ skm_status stage_docs(skm_ctx *ctx, const skm_csr *docs, DevCsr &out) {
     return SKM_OK;
 }
 
-// Resident centroid matrices for vocabulary size d (contents zeroed when (re)allocated).
-skm_status ensure_centroids(skm_ctx *ctx, int32_t d, bool zero) {
+// Resident centroid matrices for vocabulary size d (contents zeroed when (re)allocated). The
+// compacted moved-centroid matrix is needed only by the Lloyd loop and the update (with_cm);
+// a context that only assigns against loaded centroids does not hold it.
+skm_status ensure_centroids(skm_ctx *ctx, int32_t d, bool zero, bool with_cm) {
     const int32_t k = ctx->cfg.k;
     const size_t n = (size_t)d * (size_t)ctx->ldc;
+    const size_t cm_bytes = n * (ctx->cfg.precision == SKM_BF16 ? 2 : 4);
     const bool fresh = ctx->d != d || !ctx->C32.p;
     SKM_TRY(ensure(ctx, ctx->C32, n * sizeof(float)));
     if (ctx->cfg.precision == SKM_BF16) SKM_TRY(ensure(ctx, ctx->C16, n * sizeof(__nv_bfloat16)));
-    SKM_TRY(ensure(ctx, ctx->CM, n * (ctx->cfg.precision == SKM_BF16 ? 2 : 4)));
+    const void *cm_before = ctx->CM.p;
+    if (with_cm) SKM_TRY(ensure(ctx, ctx->CM, cm_bytes));
     SKM_TRY(ensure(ctx, ctx->norm_store, sizeof(double) * k));
     SKM_TRY(ensure(ctx, ctx->sq_store, sizeof(double) * k));
     if (fresh || zero) {
         SKM_CUDA(cudaMemsetAsync(ctx->C32.p, 0, n * sizeof(float), ctx->st));
         if (ctx->C16.p) SKM_CUDA(cudaMemsetAsync(ctx->C16.p, 0, n * sizeof(__nv_bfloat16), ctx->st));
-        SKM_CUDA(cudaMemsetAsync(ctx->CM.p, 0, n * (ctx->cfg.precision == SKM_BF16 ? 2 : 4), ctx->st));
         SKM_CUDA(cudaMemsetAsync(ctx->norm_store.p, 0, sizeof(double) * k, ctx->st));
         SKM_CUDA(cudaMemsetAsync(ctx->sq_store.p, 0, sizeof(double) * k, ctx->st));
     }
+    if (with_cm && (fresh || zero || ctx->CM.p != cm_before))
+        SKM_CUDA(cudaMemsetAsync(ctx->CM.p, 0, cm_bytes, ctx->st));
     ctx->d = d;
     return SKM_OK;
 }
@@ -751,7 +756,7 @@ skm_status skm_fit(skm_ctx *ctx, const skm_csr *docs, const int32_t *init_doc_id
     DevCsr dc{};
     SKM_TRY(stage_docs(ctx, docs, dc));
     const int64_t N = dc.n;
-    SKM_TRY(ensure_centroids(ctx, dc.d, true));
+    SKM_TRY(ensure_centroids(ctx, dc.d, true, true));
     SKM_TRY(ensure_cluster_bufs(ctx));
     SKM_TRY(ensure_doc_bufs(ctx, N));
     SKM_TRY(ensure(ctx, ctx->obj, sizeof(double) * ctx->cfg.max_iter));
@@ -923,7 +928,7 @@ skm_status skm_update(skm_ctx *ctx, const skm_csr *docs, const int32_t *assign, 
     for (int64_t i = 0; i < N; ++i)
         if (ha[i] < 0 || ha[i] >= k) return fail(ctx, SKM_ERR_INVALID, "assign[%lld] = %d out of range", (long long)i, ha[i]);
     const bool fresh = ctx->d != dc.d;
-    SKM_TRY(ensure_centroids(ctx, dc.d, fresh));
+    SKM_TRY(ensure_centroids(ctx, dc.d, fresh, true));
     SKM_TRY(ensure_cluster_bufs(ctx));
     SKM_TRY(ensure(ctx, ctx->obj, sizeof(double) * std::max(1, ctx->cfg.max_iter)));
     Postings pg;
@@ -942,7 +947,7 @@ skm_status skm_set_centroids(skm_ctx *ctx, int32_t n_terms, const float *centroi
     DeviceGuard g(ctx->cfg.device);
     if (n_terms < 1 || !centroids) return fail(ctx, SKM_ERR_INVALID, "n_terms >= 1 and centroids required");
     const int32_t k = ctx->cfg.k;
-    SKM_TRY(ensure_centroids(ctx, n_terms, true));
+    SKM_TRY(ensure_centroids(ctx, n_terms, true, false));
     SKM_CUDA(cudaMemcpy2DAsync(ctx->C32.p, sizeof(float) * ctx->ldc, centroids, sizeof(float) * k,
                                sizeof(float) * k, n_terms,
                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->st));

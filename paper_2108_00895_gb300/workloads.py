@@ -119,3 +119,44 @@ class BatchedWorkload:
 # Batched form: 256 uneven instances, 20 Lloyd steps each, FP32.
 BATCHED = BatchedWorkload("batched-fp32 256 instances", 256, 1000, 200_000, (20_000, 50_000, 100_000), 16, 2048,
                           80.0, 1.1, 20, 4)
+
+
+@dataclass(frozen=True)
+class ServingWorkload:
+    """Serving form: a resident BF16 centroid set (k, d) under a device budget; Poisson
+    arrivals at `rate` per second, a fraction `p_assign` of them assignment requests of
+    log-uniform [1, assign_hi] new documents (drawn from a pool of documents like the large
+    workload's), the rest clustering jobs of log-uniform N in [job_n_lo, job_n_hi] and k in
+    [job_k_lo, job_k_hi] for `job_iters` steps."""
+    name: str
+    k: int
+    n_terms: int
+    budget_gb: float
+    rate: float
+    p_assign: float
+    assign_hi: int
+    job_n_lo: int
+    job_n_hi: int
+    job_k_lo: int
+    job_k_hi: int
+    job_iters: int
+    pool_docs: int
+    nnz_mean: float
+    zipf_s: float
+    seed: int
+
+    def pool(self):
+        return synth.make_corpus(self.pool_docs, self.n_terms, self.nnz_mean, 5, 2000, self.zipf_s, 1000 + self.seed)
+
+    def describe(self) -> dict:
+        return {"workload": self.name, "k": self.k, "n_terms": self.n_terms, "budget_GB": self.budget_gb,
+                "rate_per_s": self.rate, "assign_fraction": self.p_assign,
+                "assign_docs": f"log-uniform [1, {self.assign_hi}]",
+                "job_n": f"log-uniform [{self.job_n_lo}, {self.job_n_hi}]",
+                "job_k": f"log-uniform [{self.job_k_lo}, {self.job_k_hi}]", "job_iters": self.job_iters,
+                "documents": f"lognormal(mean {self.nnz_mean:g}) clipped to [5,2000], Zipf(s={self.zipf_s:g}), "
+                             f"pool of {self.pool_docs} seeded documents"}
+
+
+SERVING = ServingWorkload("serving bf16 k=10000 d=250000", 10_000, 250_000, 40.0, 2000.0, 0.9, 4096,
+                          10_000, 500_000, 64, 4096, 20, 500_000, 150.0, 1.05, 5)
