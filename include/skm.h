@@ -79,10 +79,16 @@ typedef struct {
     skm_free_fn free;
     void *alloc_user;
     int32_t timing;       /* 1: record CUDA events around each kernel (see skm_stats) */
+    int32_t sparse_div;   /* rows of the scored centroid matrix with at most k / sparse_div
+                             nonzeros (terms present in few clusters) are stored as lists of
+                             their nonzeros, the inverted index of Sec. 3.2, and the scoring
+                             pass reads those lists instead of the dense rows. Scores and
+                             results are bit-identical either way. 0 = off (the default);
+                             used for k >= 64 */
 } skm_config;
 
 /* Fills a config with defaults: FP32, no pruning, max_iter 20, shift test off, rescoring
- * on with tau 0, no budget, device 0, default stream, cudaMalloc. */
+ * on with tau 0, no budget, device 0, default stream, cudaMalloc, sparse rows off. */
 SKM_API void skm_config_default(skm_config *cfg, int32_t k);
 
 typedef struct {
@@ -112,6 +118,11 @@ typedef struct {
     double ms_update;           /* centroid update kernels */
     int64_t launches_score;     /* scoring kernel launches */
     int64_t launches_total;     /* all kernel launches of the library */
+    int64_t fmas_exec;          /* multiply-adds executed by the scoring passes: fmas less the
+                                   products with exact zeros that sparse rows skip */
+    double ms_index;            /* device time building the sparse-row index */
+    int64_t sparse_rows;        /* rows of the centroid matrix stored by their nonzeros */
+    int64_t sparse_entries;     /* nonzeros stored for them */
 } skm_stats;
 
 /* Create a context on cfg->device. cfg is copied. */

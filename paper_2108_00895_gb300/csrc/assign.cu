@@ -44,6 +44,47 @@ __global__ void __launch_bounds__(256) k_score(ScoreArgs a) {
     }
 }
 
+// k_score with sparse rows: a KS-float scratch and a list staging buffer per warp (dynamic
+// shared memory); registers are capped so that four blocks stay resident, as for k_score.
+template <typename CT, int NV, bool COLLECT>
+__global__ void __launch_bounds__(256, 4) k_score_sparse(ScoreArgs a, SparseArgs sp) {
+    constexpr int EPV = 16 / (int)sizeof(CT);   // elements per 16-byte vector
+    constexpr int J = NV * EPV;                  // columns per lane
+    constexpr int KS = 32 * J;                   // columns per slice
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int pos = blockIdx.x * 8 + wib;
+    if (pos >= a.n_list) return;
+    const int slice = blockIdx.y;
+    const int64_t i = a.doc_list ? (int64_t)a.doc_list[pos] : (int64_t)pos;
+    const int64_t j0 = (int64_t)slice * KS;
+    const CT *Cs = reinterpret_cast<const CT *>(a.C) + j0 + lane * EPV;
+    __shared__ int2 stage[8][32];
+    extern __shared__ float4 scratch4[];
+    float2 acc[J / 2];
+    {
+        RareSlice rs;
+        rs.ptr = sp.ptr;
+        rs.ent = sp.ent;
+        rs.n_slices = sp.n_slices;
+        rs.slice = slice;
+        rs.cols = (int)min((int64_t)KS, (int64_t)a.ncols - j0);
+        rs.sacc = reinterpret_cast<float *>(scratch4) + wib * (KS + RARE_SPARE);
+        rs.stg = reinterpret_cast<char *>(scratch4) + sizeof(float) * 8 * (KS + RARE_SPARE) + wib * RARE_STAGE_BYTES;
+        slice_accumulate_sparse<CT, NV>(a.row_ptr[i], a.row_ptr[i + 1], a.col, a.val, Cs, a.ldc, stage[wib], lane,
+                                        acc, rs);
+        if (sp.skipped && rs.skipped && lane == 0)
+            atomicAdd(sp.skipped + ((pos + slice) & (SKIP_COUNTERS - 1)), rs.skipped);
+    }
+    if constexpr (COLLECT) {
+        slice_collect<CT, NV>(acc, j0, lane, a.ncols, a.col_ids, a.thr[pos], a.cand_cnt + pos,
+                              a.cand + (int64_t)pos * a.cap, a.cap);
+    } else {
+        slice_topt_write<CT, NV>(acc, j0, lane, a.ncols, a.col_ids, a.part_s, a.part_j,
+                                 ((int64_t)slice * a.n_list + pos) * TOPT);
+    }
+}
+
 int slice_width(int precision, int k) {
     // Columns per scoring slice: 32 lanes x NV 16-byte vectors. FP32: 128/256/512 for NV
     // 1/2/4; BF16: 256/512/1024. Small k uses the narrowest shape so that padded columns
@@ -58,38 +99,47 @@ int slice_width(int precision, int k) {
 }
 
 template <bool COLLECT>
-static cudaError_t launch_score_t(const ScoreArgs &a, int precision, int slice_cols, cudaStream_t st) {
+static cudaError_t launch_score_t(const ScoreArgs &a, int precision, int slice_cols, cudaStream_t st,
+                                  const SparseArgs *sp) {
     if (a.n_list <= 0) return cudaSuccess;
     const int n_slices = (a.ncols + slice_cols - 1) / slice_cols;
     if (n_slices <= 0) return cudaSuccess;
     dim3 grid((a.n_list + 7) / 8, n_slices);
+    // sparse rows need a KS-float scratch and a list staging buffer per warp
+    const size_t smem = 8 * (sizeof(float) * ((size_t)slice_cols + RARE_SPARE) + RARE_STAGE_BYTES);
+#define SKM_SCORE(CT, NVV)                                                          \
+    if (sp) k_score_sparse<CT, NVV, COLLECT><<<grid, 256, smem, st>>>(a, *sp);      \
+    else k_score<CT, NVV, COLLECT><<<grid, 256, 0, st>>>(a);                         \
+    break
     if (precision == 0) {
         switch (slice_cols) {
-            case 128: k_score<float, 1, COLLECT><<<grid, 256, 0, st>>>(a); break;
-            case 256: k_score<float, 2, COLLECT><<<grid, 256, 0, st>>>(a); break;
-            case 512: k_score<float, 4, COLLECT><<<grid, 256, 0, st>>>(a); break;
+            case 128: SKM_SCORE(float, 1);
+            case 256: SKM_SCORE(float, 2);
+            case 512: SKM_SCORE(float, 4);
             default: return cudaErrorInvalidValue;
         }
     } else {
         switch (slice_cols) {
-            case 256: k_score<__nv_bfloat16, 1, COLLECT><<<grid, 256, 0, st>>>(a); break;
-            case 512: k_score<__nv_bfloat16, 2, COLLECT><<<grid, 256, 0, st>>>(a); break;
-            case 1024: k_score<__nv_bfloat16, 4, COLLECT><<<grid, 256, 0, st>>>(a); break;
+            case 256: SKM_SCORE(__nv_bfloat16, 1);
+            case 512: SKM_SCORE(__nv_bfloat16, 2);
+            case 1024: SKM_SCORE(__nv_bfloat16, 4);
             default: return cudaErrorInvalidValue;
         }
     }
+#undef SKM_SCORE
     return cudaGetLastError();
 }
 
-cudaError_t launch_score(const ScoreArgs &a, int precision, int slice_cols, cudaStream_t st) {
-    return launch_score_t<false>(a, precision, slice_cols, st);
+cudaError_t launch_score(const ScoreArgs &a, int precision, int slice_cols, cudaStream_t st, const SparseArgs *sp) {
+    return launch_score_t<false>(a, precision, slice_cols, st, sp);
 }
 
 // Collect pass: the scoring pass again (bit-identical scores) for documents whose
 // candidate set did not fit in the top list; appends every centroid at or above the
 // document's threshold.
-cudaError_t launch_collect(const ScoreArgs &a, int precision, int slice_cols, cudaStream_t st) {
-    return launch_score_t<true>(a, precision, slice_cols, st);
+cudaError_t launch_collect(const ScoreArgs &a, int precision, int slice_cols, cudaStream_t st,
+                           const SparseArgs *sp) {
+    return launch_score_t<true>(a, precision, slice_cols, st, sp);
 }
 
 // ------------------------------------------------------------------------------------

@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "skm.h"
+#include "skm_host.h"
 
 namespace {
 
@@ -84,7 +85,11 @@ size_t fit_estimate(const skm_csr &d, int32_t k, int precision) {
     const size_t slices = (ldc + slice - 1) / slice;
     const size_t per_doc = n * (4 * 2 + 4 * 2 + 1 + 4 * 2 + 4 * 6 + 4 * 64 + 4) + n * slices * 4 * 8;
     const size_t per_clus = (size_t)k * 128;
-    return (cent + docs + post + per_doc + per_clus) * 11 / 10 + (size_t(64) << 20);
+    // sparse-row index of C and of the moved-centroid matrix: a row of either has at most
+    // df_t nonzeros, so each holds at most nnz entries; plus the marked column stream
+    const size_t esz = precision == SKM_BF16 ? 4 : 8;
+    const size_t sparse = e * (4 + 2 * esz) + t * (9 + 2 * (slices + 1) * 4);
+    return (cent + docs + post + per_doc + per_clus + sparse) * 11 / 10 + (size_t(64) << 20);
 }
 
 void assign_worker(skm_server *S) {
@@ -284,10 +289,12 @@ SKM_API skm_status skm_server_create(const skm_server_config *cfg, skm_ctx *resi
         (cfg->job_precision != SKM_FP32 && cfg->job_precision != SKM_BF16) || !(cfg->rescore_tau >= 0.0))
         return SKM_ERR_INVALID;
     if (skm_n_terms(resident) < 1) return SKM_ERR_STATE;
-    // memory kept for the resident context: what it holds now plus the per-document and
-    // staging buffers of a largest batch (they grow on demand up to this size)
+    if (skm_prepare_assign(resident) != SKM_OK) return SKM_ERR_CUDA;
+    // memory kept for the resident context: what it holds now (centroids and their
+    // sparse-row index) plus the per-document, staging and marked-column buffers of a
+    // largest batch (they grow on demand up to this size)
     const size_t nd = (size_t)cfg->max_batch_docs, ne = (size_t)cfg->max_batch_nnz;
-    const size_t reserve = skm_mem_used(resident) + ((nd + 1) * 8 + ne * 8 + nd * (48 + 4 * 64 + 32 * 32)) * 11 / 10 +
+    const size_t reserve = skm_mem_used(resident) + ((nd + 1) * 8 + ne * 12 + nd * (48 + 4 * 64 + 32 * 32)) * 11 / 10 +
                            (size_t(64) << 20);
     if (reserve > cfg->mem_budget) return SKM_ERR_BUDGET;
     skm_server *S = new skm_server();

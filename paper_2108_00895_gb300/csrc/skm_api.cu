@@ -6,11 +6,13 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
 
 #include "skm.h"
+#include "skm_host.h"
 #include "skm_kernels.cuh"
 
 using namespace skm;
@@ -67,8 +69,18 @@ struct skm_ctx {
     unsigned long long *h_counters64 = nullptr;
     double *h_scal = nullptr;
 
+    // sparse-row index of the scoring matrices (C, and CM for the pruned pass): rows of C with
+    // at most k / rare_div nonzeros; cent_epoch counts centroid changes, docs_epoch stagings
+    Buf rflag, rtot, rbase, rptr_c, rent_c, rptr_m, rent_m, colm, skipped;
+    int rare_div = 0;
+    int64_t cent_epoch = 1, docs_epoch = 0;
+    int64_t rare_c_epoch = 0, rare_m_epoch = 0, colm_epoch = 0, colm_docs = -1;
+    int32_t rare_m_ncols = -1;
+    int64_t rare_c_rows = 0, rare_c_entries = 0;
+    std::vector<uint32_t> h_rtot;
+
     skm_stats stats{};
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_score, ev_decide, ev_update;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_score, ev_decide, ev_update, ev_index;
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_next = 0;
 };
@@ -181,6 +193,7 @@ void collect_times(skm_ctx *ctx) {
     ctx->stats.ms_score += sum(ctx->ev_score);
     ctx->stats.ms_decide += sum(ctx->ev_decide);
     ctx->stats.ms_update += sum(ctx->ev_update);
+    ctx->stats.ms_index += sum(ctx->ev_index);
     ctx->ev_next = 0;
 }
 
@@ -201,6 +214,23 @@ skm_status read_counters(skm_ctx *ctx) {
 skm_status reset_counters(skm_ctx *ctx) {
     SKM_CUDA(cudaMemsetAsync(ctx->counters.p, 0, CNT_N * sizeof(int32_t), ctx->st));
     SKM_CUDA(cudaMemsetAsync(ctx->counters64.p, 0, C64_N * sizeof(unsigned long long), ctx->st));
+    return SKM_OK;
+}
+
+// Partial counts of the multiply-adds by exact zeros that sparse rows skip.
+skm_status reset_skipped(skm_ctx *ctx) {
+    SKM_TRY(ensure(ctx, ctx->skipped, sizeof(unsigned long long) * SKIP_COUNTERS));
+    SKM_CUDA(cudaMemsetAsync(ctx->skipped.p, 0, sizeof(unsigned long long) * SKIP_COUNTERS, ctx->st));
+    return SKM_OK;
+}
+
+skm_status read_skipped(skm_ctx *ctx, int64_t *out) {
+    unsigned long long h[SKIP_COUNTERS];
+    SKM_CUDA(cudaMemcpyAsync(h, ctx->skipped.p, sizeof h, cudaMemcpyDeviceToHost, ctx->st));
+    SKM_TRY(sync(ctx));
+    unsigned long long t = 0;
+    for (unsigned long long v : h) t += v;
+    *out = (int64_t)t;
     return SKM_OK;
 }
 
@@ -225,6 +255,7 @@ skm_status stage_docs(skm_ctx *ctx, const skm_csr *docs, DevCsr &out) {
     out.n = docs->n_docs;
     out.d = docs->n_terms;
     out.nnz = docs->nnz;
+    ctx->docs_epoch++;
     if (docs->on_device) {
         int64_t ends[2];
         SKM_CUDA(cudaMemcpyAsync(&ends[0], docs->row_ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->st));
@@ -293,6 +324,7 @@ skm_status ensure_centroids(skm_ctx *ctx, int32_t d, bool zero, bool with_cm) {
     if (with_cm && (fresh || zero || ctx->CM.p != cm_before))
         SKM_CUDA(cudaMemsetAsync(ctx->CM.p, 0, cm_bytes, ctx->st));
     ctx->d = d;
+    ctx->cent_epoch++;
     return SKM_OK;
 }
 
@@ -422,6 +454,109 @@ skm_status build_postings(skm_ctx *ctx, const DevCsr &dc, Postings &pg) {
     return SKM_OK;
 }
 
+// Sparse rows of the scoring matrix of one pass (off: every row dense, plain column ids).
+struct RareView {
+    const int32_t *col = nullptr;   // column stream with sparse rows marked ~t
+    const uint32_t *ptr = nullptr;
+    const void *ent = nullptr;
+    int32_t n_slices = 0;
+};
+
+// Builds, when stale, the sparse-row index of C (rows with at most k / rare_div nonzeros)
+// and the marked column stream of the staged documents; for a pruned pass also the index
+// of the compacted moved-centroid matrix CM over the same rows. The scores do not depend
+// on which rows are sparse, so the index only has to describe the current matrices.
+skm_status rare_index(skm_ctx *ctx, Buf &M, int32_t ncols, const uint8_t *only, bool classify, Buf &ptr, Buf &ent,
+                      int64_t *rows_out, int64_t *entries_out) {
+    const int32_t d = ctx->d;
+    const int prec = ctx->cfg.precision;
+    const int32_t S = (ncols + ctx->slice - 1) / ctx->slice;
+    const uint32_t thr = (uint32_t)(ctx->cfg.k / std::max(ctx->rare_div, 1));
+    SKM_TRY(ensure(ctx, ctx->rtot, sizeof(uint32_t) * d));
+    SKM_TRY(ensure(ctx, ctx->rbase, sizeof(uint32_t) * d));
+    SKM_TRY(ensure(ctx, ptr, sizeof(uint32_t) * (size_t)d * (S + 1)));
+    SKM_CUDA(launch_rare_count(M.p, prec, ctx->ldc, d, ncols, ctx->slice, thr, only,
+                               classify ? P<uint8_t>(ctx->rflag) : nullptr, P<uint32_t>(ctx->rtot), ctx->st));
+    ctx->h_rtot.resize(d);
+    SKM_CUDA(cudaMemcpyAsync(ctx->h_rtot.data(), ctx->rtot.p, sizeof(uint32_t) * d, cudaMemcpyDeviceToHost, ctx->st));
+    SKM_TRY(sync(ctx));
+    // exclusive scan on the host (d entries); the index uses 32-bit offsets
+    uint64_t tot = 0;
+    int64_t rows = 0;
+    for (int32_t t = 0; t < d; ++t) {
+        const uint32_t c = ctx->h_rtot[t];
+        ctx->h_rtot[t] = (uint32_t)tot;
+        tot += c;
+        rows += c > 0;
+        if (tot > 0xffffffffull) return fail(ctx, SKM_ERR_INVALID, "sparse-row index exceeds 2^32 entries");
+    }
+    const size_t esz = prec == SKM_BF16 ? 4 : 8;
+    SKM_TRY(ensure(ctx, ent, esz * (size_t)std::max<uint64_t>(tot, 1)));
+    SKM_CUDA(cudaMemcpyAsync(ctx->rbase.p, ctx->h_rtot.data(), sizeof(uint32_t) * d, cudaMemcpyHostToDevice, ctx->st));
+    SKM_CUDA(launch_rare_fill(M.p, prec, ctx->ldc, d, ncols, ctx->slice, S, P<uint8_t>(ctx->rflag),
+                              P<uint32_t>(ctx->rbase), P<uint32_t>(ptr), ent.p, ctx->st));
+    SKM_TRY(sync(ctx));   // h_rtot is reused by the next build
+    ctx->stats.launches_total += 2;
+    if (rows_out) *rows_out = rows;
+    if (entries_out) *entries_out = (int64_t)tot;
+    return SKM_OK;
+}
+
+skm_status build_c_index(skm_ctx *ctx) {
+    if (ctx->rare_div <= 0 || ctx->rare_c_epoch == ctx->cent_epoch) return SKM_OK;
+    SKM_TRY(ensure(ctx, ctx->rflag, (size_t)ctx->d));
+    Buf &C = ctx->cfg.precision == SKM_BF16 ? ctx->C16 : ctx->C32;
+    SKM_TRY(rare_index(ctx, C, ctx->cfg.k, nullptr, true, ctx->rptr_c, ctx->rent_c, &ctx->rare_c_rows,
+                       &ctx->rare_c_entries));
+    ctx->rare_c_epoch = ctx->cent_epoch;
+    ctx->rare_m_epoch = 0;
+    return SKM_OK;
+}
+
+skm_status ensure_rare(skm_ctx *ctx, const DevCsr &dc, bool pruned, int32_t ncols, RareView &rv) {
+    rv = RareView{};
+    if (ctx->rare_div <= 0) return SKM_OK;
+    Timed tm(ctx, ctx->ev_index);
+    SKM_TRY(build_c_index(ctx));
+    if (ctx->colm_epoch != ctx->rare_c_epoch || ctx->colm_docs != ctx->docs_epoch) {
+        SKM_TRY(ensure(ctx, ctx->colm, sizeof(int32_t) * (size_t)dc.nnz));
+        SKM_CUDA(launch_mark_rare(dc.col, dc.nnz, P<uint8_t>(ctx->rflag), P<int32_t>(ctx->colm), ctx->st));
+        ctx->stats.launches_total++;
+        ctx->colm_epoch = ctx->rare_c_epoch;
+        ctx->colm_docs = ctx->docs_epoch;
+    }
+    ctx->stats.sparse_rows = ctx->rare_c_rows;
+    ctx->stats.sparse_entries = ctx->rare_c_entries;
+    rv.col = P<int32_t>(ctx->colm);
+    if (!pruned) {
+        rv.ptr = P<uint32_t>(ctx->rptr_c);
+        rv.ent = ctx->rent_c.p;
+        rv.n_slices = (ctx->cfg.k + ctx->slice - 1) / ctx->slice;
+        return SKM_OK;
+    }
+    if (ctx->rare_m_epoch != ctx->cent_epoch || ctx->rare_m_ncols != ncols) {
+        SKM_TRY(rare_index(ctx, ctx->CM, ncols, P<uint8_t>(ctx->rflag), false, ctx->rptr_m, ctx->rent_m, nullptr,
+                           nullptr));
+        ctx->rare_m_epoch = ctx->cent_epoch;
+        ctx->rare_m_ncols = ncols;
+    }
+    rv.ptr = P<uint32_t>(ctx->rptr_m);
+    rv.ent = ctx->rent_m.p;
+    rv.n_slices = (ncols + ctx->slice - 1) / ctx->slice;
+    return SKM_OK;
+}
+
+// Points the pass at the marked column stream; returns the sparse rows (null: dense pass).
+const SparseArgs *apply_rare(skm_ctx *ctx, const RareView &rv, ScoreArgs &sa, SparseArgs &sp) {
+    if (!rv.ptr) return nullptr;
+    sa.col = rv.col;
+    sp.ptr = rv.ptr;
+    sp.ent = rv.ent;
+    sp.n_slices = rv.n_slices;
+    sp.skipped = ctx->skipped.p ? P<unsigned long long>(ctx->skipped) : nullptr;
+    return &sp;
+}
+
 // Scoring pass over a document list (nullable = all) against all k or the moved list,
 // followed by the decision kernel.
 skm_status score_and_decide(skm_ctx *ctx, const DevCsr &dc, const int32_t *list, int32_t n_list,
@@ -449,9 +584,13 @@ skm_status score_and_decide(skm_ctx *ctx, const DevCsr &dc, const int32_t *list,
     sa.part_s = P<float>(ctx->part_s);
     sa.part_j = P<int32_t>(ctx->part_j);
     const int n_slices = (sa.ncols + ctx->slice - 1) / ctx->slice;
+    RareView rv;
+    SparseArgs spa{};
+    SKM_TRY(ensure_rare(ctx, dc, pruned, sa.ncols, rv));
+    const SparseArgs *sp = apply_rare(ctx, rv, sa, spa);
     {
         Timed tm(ctx, ctx->ev_score);
-        SKM_CUDA(launch_score(sa, prec, ctx->slice, ctx->st));
+        SKM_CUDA(launch_score(sa, prec, ctx->slice, ctx->st, sp));
     }
     ctx->stats.launches_score++;
     ctx->stats.launches_total++;
@@ -534,7 +673,11 @@ skm_status rescore_queues(skm_ctx *ctx, const DevCsr &dc, int32_t *a_new, float 
         sa.cand_cnt = P<int32_t>(ctx->cand_cnt);
         sa.cand = P<int32_t>(ctx->cand);
         sa.cap = kCollectCap;
-        SKM_CUDA(launch_collect(sa, ctx->cfg.precision, ctx->slice, ctx->st));
+        RareView rv;
+        SparseArgs spa{};
+        SKM_TRY(ensure_rare(ctx, dc, false, ctx->cfg.k, rv));
+        const SparseArgs *sp = apply_rare(ctx, rv, sa, spa);
+        SKM_CUDA(launch_collect(sa, ctx->cfg.precision, ctx->slice, ctx->st, sp));
         ra.count = nullptr;
         ra.n_fixed = nb;
         ra.rs_doc = sa.doc_list;
@@ -633,6 +776,7 @@ skm_status update_step(skm_ctx *ctx, const DevCsr &dc, const Postings &pg, const
         SKM_CUDA(launch_update_write(u, ctx->st));
         SKM_CUDA(launch_from_u128(nullptr, u.sq128, n_moved, pg.F, nullptr, nullptr, P<double>(ctx->newsq), ctx->st));
         ctx->stats.launches_total += 8;
+        ctx->cent_epoch++;
     }
     // with no moved cluster pos_in_m is -1 everywhere and the objective is sum_j ||S_j||
     SKM_CUDA(launch_finish(P<int32_t>(ctx->pos_in_m), P<int32_t>(ctx->sizes), k,
@@ -664,6 +808,7 @@ void skm_config_default(skm_config *cfg, int32_t k) {
     cfg->shift_tol = -1.0;
     cfg->rescore = 1;
     cfg->rescore_tau = 0.0;
+    cfg->sparse_div = 0;
 }
 
 skm_status skm_create(const skm_config *cfg, skm_ctx **out) {
@@ -671,7 +816,7 @@ skm_status skm_create(const skm_config *cfg, skm_ctx **out) {
     *out = nullptr;
     if (cfg->k < 1 || cfg->max_iter < 1 || (cfg->precision != SKM_FP32 && cfg->precision != SKM_BF16) ||
         (cfg->prune != SKM_PRUNE_NONE && cfg->prune != SKM_PRUNE_NCC) || !(cfg->rescore_tau >= 0.0) ||
-        (cfg->alloc == nullptr) != (cfg->free == nullptr))
+        (cfg->alloc == nullptr) != (cfg->free == nullptr) || cfg->sparse_div < 0)
         return SKM_ERR_INVALID;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
@@ -684,6 +829,7 @@ skm_status skm_create(const skm_config *cfg, skm_ctx **out) {
     ctx->st = (cudaStream_t)cfg->stream;
     ctx->slice = slice_width(cfg->precision, cfg->k);
     ctx->ldc = ((int64_t)cfg->k + ctx->slice - 1) / ctx->slice * ctx->slice;
+    ctx->rare_div = cfg->k >= 64 ? cfg->sparse_div : 0;
     if (ensure(ctx, ctx->counters, CNT_N * sizeof(int32_t)) != SKM_OK ||
         ensure(ctx, ctx->counters64, C64_N * sizeof(unsigned long long)) != SKM_OK ||
         cudaMallocHost(&ctx->h_counters64, C64_N * sizeof(unsigned long long)) != cudaSuccess ||
@@ -709,6 +855,8 @@ skm_status skm_destroy(skm_ctx *ctx) {
                   &ctx->rs_cand, &ctx->refull, &ctx->full64, &ctx->collect_doc, &ctx->collect_thr, &ctx->cand,
                   &ctx->cand_cnt, &ctx->changed, &ctx->sizes, &ctx->moved,
                   &ctx->pos_in_m, &ctx->normsq, &ctx->inv_norm, &ctx->dot_fx, &ctx->newsq,
+                  &ctx->rflag, &ctx->rtot, &ctx->rbase, &ctx->rptr_c, &ctx->rent_c, &ctx->rptr_m, &ctx->rent_m,
+                  &ctx->colm, &ctx->skipped,
                   &ctx->normsq128, &ctx->sq128, &ctx->sq_store, &ctx->counters, &ctx->counters64, &ctx->scal,
                   &ctx->obj, &ctx->init_ids};
     for (Buf *b : all) release(ctx, *b);
@@ -721,6 +869,14 @@ skm_status skm_destroy(skm_ctx *ctx) {
 }
 
 const char *skm_last_error(const skm_ctx *ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
+
+skm_status skm_prepare_assign(skm_ctx *ctx) {
+    if (!ctx) return SKM_ERR_INVALID;
+    DeviceGuard g(ctx->cfg.device);
+    if (ctx->d == 0 || !ctx->C32.p) return SKM_OK;
+    SKM_TRY(build_c_index(ctx));
+    return sync(ctx);
+}
 
 int32_t skm_n_terms(const skm_ctx *ctx) { return ctx ? ctx->d : 0; }
 
@@ -768,6 +924,8 @@ skm_status skm_fit(skm_ctx *ctx, const skm_csr *docs, const int32_t *init_doc_id
                                    ctx->cfg.precision == SKM_BF16 ? P<__nv_bfloat16>(ctx->C16) : nullptr,
                                    ctx->ldc, P<double>(ctx->sq_store), ctx->st));
     ctx->stats.launches_total++;
+    ctx->cent_epoch++;
+    SKM_TRY(reset_skipped(ctx));
     SKM_CUDA(cudaMemsetAsync(ctx->clean.p, 0, N, ctx->st));
     SKM_CUDA(cudaMemsetAsync(ctx->changed.p, 1, k, ctx->st));
     SKM_CUDA(launch_order_by_length(dc.row_ptr, N, P<int32_t>(ctx->order_hist), P<int32_t>(ctx->order), ctx->st));
@@ -851,6 +1009,11 @@ skm_status skm_fit(skm_ctx *ctx, const skm_csr *docs, const int32_t *init_doc_id
     SKM_TRY(sync(ctx));
     collect_times(ctx);
     ctx->stats.iters = it;
+    {
+        int64_t sk = 0;
+        SKM_TRY(read_skipped(ctx, &sk));
+        ctx->stats.fmas_exec = ctx->stats.fmas - sk;
+    }
     if (iters_out) *iters_out = it;
     return SKM_OK;
 }
@@ -870,6 +1033,7 @@ skm_status skm_assign(skm_ctx *ctx, const skm_csr *docs, int32_t *assign_out, fl
     SKM_TRY(ensure_doc_bufs(ctx, N));
     int32_t *a_new = P<int32_t>(ctx->abuf[0]);
     SKM_TRY(reset_counters(ctx));
+    SKM_TRY(reset_skipped(ctx));
     // scores go straight to a device output, or through a temporary for a host output
     float *score_dev = nullptr;
     Buf tmp_score;
@@ -900,6 +1064,11 @@ skm_status skm_assign(skm_ctx *ctx, const skm_csr *docs, int32_t *assign_out, fl
     ctx->stats.bytes = 8 * dc.nnz + 20 * N +
                        (int64_t)ctx->d * ctx->cfg.k * (ctx->cfg.precision == SKM_BF16 ? 2 : 4);
     ctx->stats.iters = 1;
+    if (s == SKM_OK) {
+        int64_t sk = 0;
+        s = read_skipped(ctx, &sk);
+        ctx->stats.fmas_exec = ctx->stats.fmas - sk;
+    }
     return s;
 }
 
@@ -955,6 +1124,7 @@ skm_status skm_set_centroids(skm_ctx *ctx, int32_t n_terms, const float *centroi
         SKM_CUDA(launch_to_bf16(P<float>(ctx->C32), P<__nv_bfloat16>(ctx->C16), (int64_t)n_terms * ctx->ldc, ctx->st));
         ctx->stats.launches_total++;
     }
+    ctx->cent_epoch++;
     SKM_CUDA(launch_col_sq(P<float>(ctx->C32), ctx->ldc, n_terms, k, P<double>(ctx->sq_store), ctx->st));
     return sync(ctx);
 }

@@ -1,6 +1,8 @@
 // Device helpers shared by the single-collection and the batched kernels (internal).
 #pragma once
 
+#include <type_traits>
+
 #include "skm_internal.cuh"
 
 namespace skm {
@@ -23,6 +25,137 @@ __device__ __forceinline__ void fma_row(float2 (&acc)[NV * 16 / (int)sizeof(CT) 
                 acc[u * 4 + h] = __ffma2_rn(vv, make_float2(bf16lo(ww[h]), bf16hi(ww[h])), acc[u * 4 + h]);
         }
     }
+}
+
+// Sparse rows of one scoring slice. A term t whose centroid row is stored sparsely arrives
+// in the column stream as ~t (negative); its nonzeros in this slice are ent[ptr[t * (n_slices
+// + 1) + slice] .. ptr[... + 1]), ascending column: (offset within the slice << 16 | BF16
+// bits) for BF16 matrices, {offset, FP32 bits} for FP32 ones; lists are padded to whole
+// 16-byte vectors with entries for offset KS, a spare scratch column.
+struct RareSlice {
+    const uint32_t *ptr = nullptr;
+    const void *ent = nullptr;
+    int32_t n_slices = 0;
+    int32_t slice = 0;
+    int32_t cols = 0;                  // valid columns of this slice
+    float *sacc = nullptr;             // the warp's scratch: one float per slice column + spare
+    void *stg = nullptr;               // the warp's list staging: RARE_STAGE_BYTES
+    unsigned long long skipped = 0;    // multiply-adds by exact zeros not executed (lane-uniform)
+};
+
+constexpr int RARE_STAGE_BYTES = 1024;
+constexpr int RARE_SPARE = 4;          // scratch floats past the slice (16-byte multiple)
+
+// Rows [q, qe) of the staged (t, x) pairs, all dense, accumulated in order; G rows are
+// loaded together.
+template <typename CT, int NV>
+__device__ __forceinline__ void dense_rows(int q, int qe, const int2 *stage, const CT *Cs, int64_t ldc,
+                                           float2 (&acc)[NV * 16 / (int)sizeof(CT) / 2]) {
+    constexpr int EPV = 16 / (int)sizeof(CT);
+    constexpr int G = NV >= 4 ? 2 : 4;
+    for (; q + G <= qe; q += G) {
+        uint4 w[G][NV];
+        float v[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int2 tv = stage[q + g];
+            v[g] = __int_as_float(tv.y);
+            const CT *row = Cs + (int64_t)tv.x * ldc;
+#pragma unroll
+            for (int u = 0; u < NV; ++u) w[g][u] = ldg16(row + u * 32 * EPV);
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) fma_row<CT, NV>(acc, v[g], w[g]);
+    }
+    for (; q < qe; ++q) {
+        const int2 tv = stage[q];
+        const CT *row = Cs + (int64_t)tv.x * ldc;
+        uint4 w[NV];
+#pragma unroll
+        for (int u = 0; u < NV; ++u) w[u] = ldg16(row + u * 32 * EPV);
+        fma_row<CT, NV>(acc, __int_as_float(tv.y), w);
+    }
+}
+
+// Rows [q0, q1) of the staged pairs, all sparse, in order. The accumulators go through the
+// warp's scratch: each nonzero (c, v) of a row updates column c with the same fused
+// multiply-add the dense form would apply, and the zeros it skips would add exactly +0,
+// so the result is bit-identical to accumulating the dense rows. Lane q holds the list
+// bounds (e0, e1) and the value x of staged row q, loaded at staging time. The lanes copy
+// their rows' lists into the staging buffer together (16-byte loads, one latency round
+// for as many rows as fit), then the rows are applied one after another from shared
+// memory; a list longer than the buffer is applied straight from global memory.
+template <typename CT, int NV>
+__device__ __forceinline__ void sparse_rows(int q0, int q1, RareSlice &rs, int lane, uint32_t e0_mine,
+                                            uint32_t e1_mine, float x_mine,
+                                            float2 (&acc)[NV * 16 / (int)sizeof(CT) / 2]) {
+    constexpr int EPV = 16 / (int)sizeof(CT);
+    using E = typename std::conditional<sizeof(CT) == 2, uint32_t, uint2>::type;
+    constexpr uint32_t EV = 16 / sizeof(E);                       // entries per vector
+    constexpr uint32_t CAP = RARE_STAGE_BYTES / sizeof(E);        // staged entries
+    const E *ent = static_cast<const E *>(rs.ent);
+    E *stg = static_cast<E *>(rs.stg);
+    auto apply = [&](const E &w, float x) {
+        if constexpr (sizeof(CT) == 2) {
+            float *p = rs.sacc + (w >> 16);
+            *p = fmaf(x, __uint_as_float(w << 16), *p);
+        } else {
+            float *p = rs.sacc + w.x;
+            *p = fmaf(x, __uint_as_float(w.y), *p);
+        }
+    };
+    float4 *mine = reinterpret_cast<float4 *>(rs.sacc + lane * EPV);
+#pragma unroll
+    for (int u = 0; u < NV; ++u)
+#pragma unroll
+        for (int h = 0; h < EPV / 4; ++h)
+            mine[u * 8 * EPV + h] = make_float4(acc[u * EPV / 2 + 2 * h].x, acc[u * EPV / 2 + 2 * h].y,
+                                                acc[u * EPV / 2 + 2 * h + 1].x, acc[u * EPV / 2 + 2 * h + 1].y);
+    __syncwarp();
+    const bool in_run = lane >= q0 && lane < q1;
+    const uint32_t len_mine = in_run ? e1_mine - e0_mine : 0u;
+    int q = q0;
+    while (q < q1) {
+        // rows [q, qc) whose lists fit in the buffer together
+        uint32_t l = lane >= q ? len_mine : 0u;
+        uint32_t incl = l;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t o = __shfl_up_sync(FULL, incl, off);
+            if (lane >= off) incl += o;
+        }
+        const unsigned over = __ballot_sync(FULL, lane >= q && lane < q1 && incl > CAP);
+        int qc = over ? __ffs(over) - 1 : q1;
+        const bool direct = qc == q;          // row q alone overflows the buffer
+        if (direct) qc = q + 1;
+        if (!direct && lane >= q && lane < qc) {
+            const uint32_t o = incl - l;
+            const uint4 *src = reinterpret_cast<const uint4 *>(ent + e0_mine);
+            uint4 *dst = reinterpret_cast<uint4 *>(stg + o);
+#pragma unroll 4
+            for (uint32_t v = 0; v < l / EV; ++v) dst[v] = __ldg(src + v);
+        }
+        __syncwarp();
+        for (int r = q; r < qc; ++r) {
+            const uint32_t len_r = __shfl_sync(FULL, l, r);
+            const uint32_t off_r = __shfl_sync(FULL, incl - l, r);
+            const uint32_t e0_r = __shfl_sync(FULL, e0_mine, r);
+            const float x_r = __shfl_sync(FULL, x_mine, r);
+            for (uint32_t e = lane; e < len_r; e += 32u) apply(direct ? __ldg(ent + e0_r + e) : stg[off_r + e], x_r);
+            if ((uint32_t)rs.cols > len_r) rs.skipped += (unsigned long long)(rs.cols - len_r);
+            __syncwarp();
+        }
+        q = qc;
+    }
+#pragma unroll
+    for (int u = 0; u < NV; ++u)
+#pragma unroll
+        for (int h = 0; h < EPV / 4; ++h) {
+            const float4 f = mine[u * 8 * EPV + h];
+            acc[u * EPV / 2 + 2 * h] = make_float2(f.x, f.y);
+            acc[u * EPV / 2 + 2 * h + 1] = make_float2(f.z, f.w);
+        }
+    __syncwarp();
 }
 
 // Scoring of one document against one slice: acc (lane's J columns, as pairs) = sum over
@@ -65,6 +198,55 @@ __device__ __forceinline__ void slice_accumulate(int64_t beg, int64_t end, const
 #pragma unroll
             for (int u = 0; u < NV; ++u) w[u] = ldg16(row + u * 32 * EPV);
             fma_row<CT, NV>(acc, __int_as_float(tv.y), w);
+        }
+    }
+}
+
+// slice_accumulate with sparse rows: negative column entries ~t mark rows stored by their
+// nonzeros (see RareSlice); runs of dense and sparse rows alternate in CSR order, so every
+// score is the one slice_accumulate computes from the dense matrix, bit for bit.
+template <typename CT, int NV>
+__device__ __forceinline__ void slice_accumulate_sparse(int64_t beg, int64_t end, const int32_t *col,
+                                                        const float *val, const CT *Cs, int64_t ldc, int2 *stage,
+                                                        int lane, float2 (&acc)[NV * 16 / (int)sizeof(CT) / 2],
+                                                        RareSlice &rs) {
+    constexpr int EPV = 16 / (int)sizeof(CT);
+    constexpr int J = NV * EPV;
+#pragma unroll
+    for (int q = 0; q < J / 2; ++q) acc[q] = make_float2(0.f, 0.f);
+    for (int64_t b = beg; b < end; b += 32) {
+        const int n = (int)min((int64_t)32, end - b);
+        __syncwarp();
+        int t_mine = 0;
+        float x_mine = 0.f;
+        uint32_t e0_mine = 0, e1_mine = 0;
+        if (lane < n) {
+            t_mine = __ldg(col + b + lane);
+            x_mine = __ldg(val + b + lane);
+            stage[lane] = make_int2(t_mine, __float_as_int(x_mine));
+            if (t_mine < 0) {
+                const uint32_t *pp = rs.ptr + (int64_t)(~t_mine) * (rs.n_slices + 1) + rs.slice;
+                e0_mine = __ldg(pp);
+                e1_mine = __ldg(pp + 1);
+            }
+        }
+        __syncwarp();
+        const unsigned rare = __ballot_sync(FULL, t_mine < 0);
+        if (rare == 0u) {
+            dense_rows<CT, NV>(0, n, stage, Cs, ldc, acc);
+            continue;
+        }
+        const unsigned valid = n >= 32 ? FULL : ((1u << n) - 1u);
+        int q = 0;
+        while (q < n) {
+            const unsigned r_from = rare & (FULL << q);
+            const int qe = r_from ? __ffs(r_from) - 1 : n;
+            dense_rows<CT, NV>(q, qe, stage, Cs, ldc, acc);
+            if (qe >= n) break;
+            const unsigned d_from = ~rare & valid & (FULL << qe);
+            const int qr = d_from ? __ffs(d_from) - 1 : n;
+            sparse_rows<CT, NV>(qe, qr, rs, lane, e0_mine, e1_mine, x_mine, acc);
+            q = qr;
         }
     }
 }

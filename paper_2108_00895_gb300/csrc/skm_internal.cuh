@@ -103,9 +103,46 @@ struct ScoreArgs {
     int32_t cap;
 };
 
+// Sparse rows of the scored matrix (see rare.cu): the column stream passed in ScoreArgs.col
+// marks a term whose row of C is stored by its nonzeros as ~t < 0; its nonzeros in slice s
+// are ent[ptr[t * (n_slices + 1) + s] .. ptr[t * (n_slices + 1) + s + 1]), ascending
+// column, each (offset within the slice << 16 | BF16 bits) for BF16 matrices and
+// {offset, FP32 bits} for FP32 ones, padded to a 16-byte multiple with entries whose
+// offset is the slice width (a spare scratch column) and value 0.
+struct SparseArgs {
+    const uint32_t *ptr;
+    const void *ent;
+    int32_t n_slices;
+    unsigned long long *skipped;   // nullable: SKIP_COUNTERS partial counts of the
+                                   // multiply-adds by exact zeros not executed
+};
+
+constexpr int SKIP_COUNTERS = 256;
+
 // Launch helpers (defined in assign.cu). Return cudaSuccess or the launch error.
-cudaError_t launch_score(const ScoreArgs &a, int precision, int slice_cols, cudaStream_t st);
-cudaError_t launch_collect(const ScoreArgs &a, int precision, int slice_cols, cudaStream_t st);
+// sp (nullable): sparse rows of the matrix, with a.col the marked column stream.
+cudaError_t launch_score(const ScoreArgs &a, int precision, int slice_cols, cudaStream_t st,
+                         const SparseArgs *sp = nullptr);
+cudaError_t launch_collect(const ScoreArgs &a, int precision, int slice_cols, cudaStream_t st,
+                           const SparseArgs *sp = nullptr);
 int slice_width(int precision, int k);   // KS for the scoring kernel
+
+// Sparse-row index (defined in rare.cu). M is a term-major d x ldc matrix (FP32 for
+// precision 0, BF16 for 1) whose first ncols columns are valid.
+// Lists are per slice of ks columns and padded to whole 16-byte vectors (4 BF16 or 2 FP32
+// entries) with entries (ks, 0) that address a spare column, so every list starts 16-byte
+// aligned.
+// rare_count: rowtot[t] = padded list length of row t over the valid columns; with flag
+//   set, flag[t] = (nonzeros of row t <= thr) and rowtot[t] is zeroed for the other rows;
+//   with only set, rows whose only[t] is 0 get rowtot[t] = 0.
+// rare_fill: for every row with flag[t], writes ptr[t * (n_slices + 1) + s] (s = 0..n_slices)
+//   from row_base[t] and the row's nonzeros, slice by slice, to ent.
+// mark_rare: colm[e] = flag[col[e]] ? ~col[e] : col[e].
+cudaError_t launch_rare_count(const void *M, int precision, int64_t ldc, int32_t d, int32_t ncols, int32_t ks,
+                              uint32_t thr, const uint8_t *only, uint8_t *flag, uint32_t *rowtot, cudaStream_t st);
+cudaError_t launch_rare_fill(const void *M, int precision, int64_t ldc, int32_t d, int32_t ncols, int32_t ks,
+                             int32_t n_slices, const uint8_t *flag, const uint32_t *row_base, uint32_t *ptr,
+                             void *ent, cudaStream_t st);
+cudaError_t launch_mark_rare(const int32_t *col, int64_t nnz, const uint8_t *flag, int32_t *colm, cudaStream_t st);
 
 }  // namespace skm

@@ -40,7 +40,8 @@ class skm_config(ctypes.Structure):
                 ("rescore", ctypes.c_int32), ("rescore_tau", ctypes.c_double),
                 ("mem_budget", ctypes.c_size_t), ("device", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
-                ("alloc_user", ctypes.c_void_p), ("timing", ctypes.c_int32)]
+                ("alloc_user", ctypes.c_void_p), ("timing", ctypes.c_int32),
+                ("sparse_div", ctypes.c_int32)]
 
 
 class skm_csr(ctypes.Structure):
@@ -56,7 +57,9 @@ class skm_stats(ctypes.Structure):
                 ("docs_rescored_full", ctypes.c_int64), ("moved_total", ctypes.c_int64),
                 ("ms_score", ctypes.c_double), ("ms_decide", ctypes.c_double),
                 ("ms_update", ctypes.c_double), ("launches_score", ctypes.c_int64),
-                ("launches_total", ctypes.c_int64)]
+                ("launches_total", ctypes.c_int64), ("fmas_exec", ctypes.c_int64),
+                ("ms_index", ctypes.c_double), ("sparse_rows", ctypes.c_int64),
+                ("sparse_entries", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -373,13 +376,15 @@ class SphericalKMeans:
     """One libskm context: exact spherical k-means on one GPU.
 
     precision: "fp32" or "bf16" (scored centroid copy); prune: "none" or "ncc"
-    (Sec. 3.1 skip); rescore: FP64 rescoring of near ties; tau: margin threshold.
+    (Sec. 3.1 skip); rescore: FP64 rescoring of near ties; tau: margin threshold;
+    sparse_div: centroid rows with at most k / sparse_div nonzeros are scored from their
+    nonzero lists (0 = off; results are identical either way).
     """
 
     def __init__(self, k: int, precision: str = "fp32", prune: str = "none", max_iter: int = 20,
                  shift_tol: float = -1.0, rescore: bool = True, tau: float = 0.0, device: int = 0,
                  stream: int | None = None, mem_budget: int = 0, timing: bool = False,
-                 allocator: str = "torch"):
+                 allocator: str = "torch", sparse_div: int = 0):
         self.lib = load()
         cfg = skm_config_default(k)
         cfg.precision = {"fp32": SKM_FP32, "bf16": SKM_BF16}[precision]
@@ -391,6 +396,7 @@ class SphericalKMeans:
         cfg.mem_budget = int(mem_budget)
         cfg.device = int(device)
         cfg.timing = int(bool(timing))
+        cfg.sparse_div = int(sparse_div)
         if stream is None and allocator == "torch":
             import torch
             stream = torch.cuda.current_stream(device).cuda_stream
