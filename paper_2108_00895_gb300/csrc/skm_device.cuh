@@ -311,15 +311,16 @@ __device__ __forceinline__ void slice_collect(const float2 (&acc)[NV * 16 / (int
 // ------------------------------------------------------------------------------------
 // Error bound of the scoring pass for one document (all data are non-negative):
 //   |s_hat - s| <= beta * s,  beta = u_c + gamma_n * (1 + u_c),
-// u_c the unit roundoff of the centroid copy (2^-9 for BF16 round-to-nearest-even, 0 for
-// the FP32 master itself) and gamma_n = n u / (1 - n u), u = 2^-24, n = nonzeros of the
-// document (one rounding per fused multiply-add).
+// u_c the unit roundoff of the centroid copy (0 for the FP32 master itself; 2^-8 for BF16
+// round-to-nearest-even: an 8-bit significand, so a value just above a power of two can
+// move by half of a 2^-7 spacing) and gamma_n = n u / (1 - n u), u = 2^-24, n = nonzeros
+// of the document (one rounding per fused multiply-add).
 // ------------------------------------------------------------------------------------
 __device__ __forceinline__ double score_beta(int precision, int64_t nnz) {
     const double u = 5.9604644775390625e-08;  // 2^-24
     const double nu = (double)nnz * u;
     const double gam = nu / (1.0 - nu);
-    const double uc = precision == 1 ? 1.953125e-03 : 0.0;  // 2^-9
+    const double uc = precision == 1 ? 3.90625e-03 : 0.0;  // 2^-8
     return uc + gam * (1.0 + uc);
 }
 

@@ -69,6 +69,28 @@ def test_assign_matches_oracle(skm, precision, k):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_bf16_worst_case_rounding_is_rescored(skm, precision):
+    """BF16 keeps an 8-bit significand, so its unit roundoff is 2^-8: a value just above a
+    midpoint above 0.5 rounds up by almost 2^-9, i.e. by 2^-8 of itself. Here centroid 0 has
+    its first coordinate rounded up that far and centroid 1 its first coordinate rounded
+    down that far; centroid 1 is exactly better by 1.6e-5, yet its BF16 score is lower by
+    0.003125, which exceeds 2 * 2^-9 * s1 but not 2 * 2^-8 * s1. Only a bound with the
+    correct unit roundoff sends the document to FP64 rescoring."""
+    h = 2.0 ** -9
+    C = np.array([[0.5 + h + 1e-6, 0.5 + h - 1e-6],
+                  [0.5, 0.5 + 3e-5]], dtype=np.float32)          # d x k: terms x centroids
+    docs = synth.Csr(np.array([0, 2], np.int64), np.array([0, 1], np.int32),
+                     np.array([0.8, 0.6], np.float32), 2)
+    a_or, s1, s2 = oracle.assign(docs, C)
+    assert a_or[0] == 1 and s1[0] - s2[0] > 1e-5
+    with skm.SphericalKMeans(2, precision=precision) as km:
+        km.set_centroids(C)
+        a, s = km.assign(docs)
+    assert a[0] == 1
+    assert abs(s[0] - s1[0]) < 1e-6       # the rescored (FP64) similarity of centroid 1
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
 def test_assign_without_rescoring_is_plain_argmax_within_error_bound(skm, precision):
     docs = _corpus(800, 3000, 40, 5, 300, 1.1, 77)
     C = _trained_centroids(docs, 64, 78)
@@ -76,7 +98,7 @@ def test_assign_without_rescoring_is_plain_argmax_within_error_bound(skm, precis
         km.set_centroids(C)
         a, _ = km.assign(docs)
     a_or, s1, s2 = oracle.assign(docs, C)
-    bound = 2.0 * (2.0 ** -9 if precision == "bf16" else 2e-4) * s1
+    bound = 2.0 * (2.0 ** -8 if precision == "bf16" else 2e-4) * s1
     clear = (s1 - s2) > bound
     np.testing.assert_array_equal(a[clear], a_or[clear])
 
