@@ -12,6 +12,10 @@ Metric: documents assigned per second per iteration (N x iterations / time).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload large|medium|small]
   python bench.py --impl reference ...   (the FP64 CPU oracle on host cores)
 
+Variants of a fit workload for comparisons and profiling (the JSON config records them):
+  --precision bf16|fp32  --prune ncc|none  --rescore on|off  --max-iter N
+  --sparse-div D (sparse centroid rows)  --case N,D,K (documents, vocabulary, clusters)
+
 Under torchrun (N > 1) each rank runs an independent replica (different seeds) on its
 own GPU; the job value is the sum of the ranks' documents over the slowest rank's time.
 """
@@ -240,8 +244,8 @@ def run_ours(args, w, world, rank, local, dist):
               torch.from_numpy(docs.values).to(dev))
     stream = torch.cuda.current_stream(dev)
     km = skm.SphericalKMeans(w.k, precision=w.precision, prune=w.prune, max_iter=w.max_iter,
-                             shift_tol=-1.0, rescore=True, tau=args.tau, device=local,
-                             stream=stream.cuda_stream, timing=True)
+                             shift_tol=-1.0, rescore=args.rescore == "on", tau=args.tau, device=local,
+                             stream=stream.cuda_stream, timing=True, sparse_div=args.sparse_div)
     a_dev = torch.empty(N, dtype=torch.int32, device=dev)
     for _ in range(args.warmup):
         km.fit(d_docs, ids, n_terms=docs.n_terms, assign_out=a_dev)
@@ -328,7 +332,7 @@ def run_ours(args, w, world, rank, local, dist):
                                step="one full clustering job (fit)", iterations_per_step=iters / args.steps,
                                l2="inputs larger than L2 (CSR + centroid matrices >> 129 MB)",
                                objective_last=float(objectives[-1]) if objectives is not None else None,
-                               tau=args.tau),
+                               tau=args.tau, rescore=args.rescore, sparse_div=args.sparse_div),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": int(agg["launches_total"]),
                 "work": {k_: v for k_, v in agg.items()}}
@@ -537,6 +541,12 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--profile-run", action="store_true",
                     help="allow fewer warm-up steps (launch lists under a profiler; not a timed number)")
+    ap.add_argument("--precision", choices=["bf16", "fp32"], default=None, help="override the workload's")
+    ap.add_argument("--prune", choices=["ncc", "none"], default=None, help="override the workload's")
+    ap.add_argument("--rescore", choices=["on", "off"], default="on", help="FP64 rescoring of near ties")
+    ap.add_argument("--max-iter", type=int, default=None, help="override the workload's step limit")
+    ap.add_argument("--sparse-div", type=int, default=0, help="sparse centroid rows (0 = off)")
+    ap.add_argument("--case", default=None, help="N,D,K: the workload's recipe at other sizes")
     args = ap.parse_args()
     if args.warmup < 3 and not args.profile_run:
         ap.error("--warmup must be >= 3 (timed numbers need three warm-up steps)")
@@ -585,6 +595,18 @@ def main():
                 dist.destroy_process_group()
         return
     w = workloads.ALL[args.workload]
+    over = {}
+    if args.precision:
+        over["precision"] = args.precision
+    if args.prune:
+        over["prune"] = args.prune
+    if args.max_iter:
+        over["max_iter"] = args.max_iter
+    if args.case:
+        n, d, k = (int(x) for x in args.case.split(","))
+        over.update(n_docs=n, n_terms=d, k=k, name=f"{w.name} scaled to N={n} d={d} k={k}")
+    if over:
+        w = w.scaled(**over)
     try:
         if args.impl == "reference":
             run_reference(args, w, world, rank, dist)
