@@ -14,7 +14,7 @@ Metric: documents assigned per second per iteration (N x iterations / time).
 
 Variants of a fit workload for comparisons and profiling (the JSON config records them):
   --precision bf16|fp32  --prune ncc|none  --rescore on|off  --max-iter N
-  --sparse-div D (sparse centroid rows)  --case N,D,K (documents, vocabulary, clusters)
+  --sparse-div D (sparse centroid rows)  --case N,D,K (documents, vocabulary, clusters)  --k K
 
 Under torchrun (N > 1) each rank runs an independent replica (different seeds) on its
 own GPU; the job value is the sum of the ranks' documents over the slowest rank's time.
@@ -244,7 +244,7 @@ def run_ours(args, w, world, rank, local, dist):
               torch.from_numpy(docs.values).to(dev))
     stream = torch.cuda.current_stream(dev)
     km = skm.SphericalKMeans(w.k, precision=w.precision, prune=w.prune, max_iter=w.max_iter,
-                             shift_tol=-1.0, rescore=args.rescore == "on", tau=args.tau, device=local,
+                             shift_tol=w.shift_tol, rescore=args.rescore == "on", tau=args.tau, device=local,
                              stream=stream.cuda_stream, timing=True, sparse_div=args.sparse_div)
     a_dev = torch.empty(N, dtype=torch.int32, device=dev)
     for _ in range(args.warmup):
@@ -533,7 +533,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["large", "medium", "small", "batched", "serving"], default="large")
+    ap.add_argument("--workload", choices=["large", "medium", "small", "tweets", "abstracts", "batched", "serving"],
+                    default="large")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving window (open loop)")
     ap.add_argument("--tau", type=float, default=1e-4)
     ap.add_argument("--no-e2e", action="store_true")
@@ -547,6 +548,7 @@ def main():
     ap.add_argument("--max-iter", type=int, default=None, help="override the workload's step limit")
     ap.add_argument("--sparse-div", type=int, default=0, help="sparse centroid rows (0 = off)")
     ap.add_argument("--case", default=None, help="N,D,K: the workload's recipe at other sizes")
+    ap.add_argument("--k", type=int, default=None, help="override the workload's number of clusters")
     args = ap.parse_args()
     if args.warmup < 3 and not args.profile_run:
         ap.error("--warmup must be >= 3 (timed numbers need three warm-up steps)")
@@ -605,6 +607,8 @@ def main():
     if args.case:
         n, d, k = (int(x) for x in args.case.split(","))
         over.update(n_docs=n, n_terms=d, k=k, name=f"{w.name} scaled to N={n} d={d} k={k}")
+    if args.k:
+        over.update(k=args.k, name=f"{over.get('name', w.name)} with k={args.k}")
     if over:
         w = w.scaled(**over)
     try:

@@ -302,12 +302,20 @@ constexpr uint32_t UPD_EMPTY = 0xffffffffu;
 constexpr int UPD_LIGHT_THREADS = 512;
 constexpr int UPD_HEAVY_THREADS = 1024;
 constexpr int UPD_TILE = 16384;               // moved entries per heavy-term tile (12 bytes each)
+constexpr int UPD_AGG = 512;                  // moved lists up to this size sum their per-cluster
+                                              // 128-bit totals in shared memory first (few
+                                              // clusters: all blocks would hit the same words)
+constexpr int UPD_PRIV = 128;                 // moved lists up to this size: warp-private
+                                              // heavy-term accumulators (UPD_TILE >= 32 x 128)
 
-// S (fixed point, 2^-F units) of entry m of term t: the norm or write step.
+// S (fixed point, 2^-F units) of entry m of term t: the norm or write step. The per-cluster
+// 128-bit sums go to agg (shared, flushed by update_flush) for short moved lists.
 template <bool WRITE>
-__device__ __forceinline__ void update_entry(const UpdateArgs &u, int32_t t, int m, unsigned long long S) {
+__device__ __forceinline__ void update_entry(const UpdateArgs &u, int32_t t, int m, unsigned long long S,
+                                             unsigned long long *agg) {
+    unsigned long long *dst = u.n_moved <= UPD_AGG ? agg + 2 * m : (WRITE ? u.sq128 : u.normsq128) + 2 * m;
     if (!WRITE) {
-        atomic_add_u128(u.normsq128 + 2 * m, S * S, __umul64hi(S, S));
+        atomic_add_u128(dst, S * S, __umul64hi(S, S));
         return;
     }
     const int32_t j = __ldg(u.moved + m);
@@ -321,17 +329,30 @@ __device__ __forceinline__ void update_entry(const UpdateArgs &u, int32_t t, int
         reinterpret_cast<float *>(u.CM)[row + m] = c;
     const double c2 = (double)c * (double)c;   // exact (24-bit mantissa squared)
     const unsigned long long q = (unsigned long long)__double2ull_rn(ldexp(c2, 62));
-    atomic_add_u128(u.sq128 + 2 * m, q, 0ull);
+    atomic_add_u128(dst, q, 0ull);
+}
+
+// Adds the block's shared per-cluster sums to the global ones (short moved lists only).
+template <bool WRITE>
+__device__ __forceinline__ void update_flush(const UpdateArgs &u, unsigned long long *agg) {
+    if (u.n_moved > UPD_AGG) return;
+    unsigned long long *dst = WRITE ? u.sq128 : u.normsq128;
+    for (int m = threadIdx.x; m < u.n_moved; m += blockDim.x) {
+        const unsigned long long lo = agg[2 * m], hi = agg[2 * m + 1];
+        if (lo | hi) atomic_add_u128(dst + 2 * m, lo, hi);
+    }
 }
 
 template <bool WRITE>
 __global__ void __launch_bounds__(UPD_LIGHT_THREADS) k_upd_light(UpdateArgs u) {
     extern __shared__ unsigned long long vals[];                         // [UPD_SLOTS]
     uint32_t *keys = reinterpret_cast<uint32_t *>(vals + UPD_SLOTS);     // [UPD_SLOTS]
+    unsigned long long *agg = reinterpret_cast<unsigned long long *>(keys + UPD_SLOTS);   // [2 * UPD_AGG]
     for (int q = threadIdx.x; q < UPD_SLOTS; q += UPD_LIGHT_THREADS) {
         keys[q] = UPD_EMPTY;
         vals[q] = 0ull;
     }
+    for (int q = threadIdx.x; q < 2 * UPD_AGG; q += UPD_LIGHT_THREADS) agg[q] = 0ull;
     __syncthreads();
     const uint32_t nm = (uint32_t)u.n_moved;
     for (int c = blockIdx.x; c < u.n_light; c += gridDim.x) {
@@ -358,25 +379,51 @@ __global__ void __launch_bounds__(UPD_LIGHT_THREADS) k_upd_light(UpdateArgs u) {
             const uint32_t key = keys[q];
             if (key == UPD_EMPTY) continue;
             const uint32_t tl = key / nm;
-            update_entry<WRITE>(u, t0 + (int32_t)tl, (int)(key - tl * nm), vals[q]);
+            update_entry<WRITE>(u, t0 + (int32_t)tl, (int)(key - tl * nm), vals[q], agg);
             keys[q] = UPD_EMPTY;
             vals[q] = 0ull;
         }
         __syncthreads();
     }
+    update_flush<WRITE>(u, agg);
 }
 
 template <bool WRITE>
 __global__ void __launch_bounds__(UPD_HEAVY_THREADS) k_upd_heavy(UpdateArgs u) {
     extern __shared__ unsigned long long acc[];                              // [UPD_TILE]
     int32_t *touched = reinterpret_cast<int32_t *>(acc + UPD_TILE);          // [UPD_TILE]
+    unsigned long long *agg = reinterpret_cast<unsigned long long *>(touched + UPD_TILE);   // [2 * UPD_AGG]
     __shared__ int32_t n_touched;
+    const int warp = threadIdx.x >> 5;
     for (int q = threadIdx.x; q < UPD_TILE; q += UPD_HEAVY_THREADS) acc[q] = 0ull;
+    for (int q = threadIdx.x; q < 2 * UPD_AGG; q += UPD_HEAVY_THREADS) agg[q] = 0ull;
     if (threadIdx.x == 0) n_touched = 0;
     __syncthreads();
     for (int h = blockIdx.x; h < u.n_heavy; h += gridDim.x) {
         const int32_t t = u.heavy_terms[h];
         const int64_t pb = u.col_ptr[t], pe = u.col_ptr[t + 1];
+        if (u.n_moved <= UPD_PRIV) {
+            // short moved list: each warp sums into its own UPD_PRIV accumulators, then the
+            // warps' partial sums are added per position (integer sums: order-free)
+            unsigned long long *mine = acc + warp * UPD_PRIV;
+            for (int64_t p = pb + threadIdx.x; p < pe; p += UPD_HEAVY_THREADS) {
+                const int m = __ldg(u.mdoc + __ldg(u.row_idx + p));
+                if (m < 0) continue;
+                const unsigned long long q = fixed_point(__ldg(u.cval + p), u.F);
+                if (q != 0ull) atomicAdd(mine + m, q);
+            }
+            __syncthreads();
+            for (int m = threadIdx.x; m < u.n_moved; m += UPD_HEAVY_THREADS) {
+                unsigned long long sum = 0ull;
+                for (int w = 0; w < UPD_HEAVY_THREADS / 32; ++w) {
+                    sum += acc[w * UPD_PRIV + m];
+                    acc[w * UPD_PRIV + m] = 0ull;
+                }
+                if (sum) update_entry<WRITE>(u, t, m, sum, agg);
+            }
+            __syncthreads();
+            continue;
+        }
         for (int m0 = 0; m0 < u.n_moved; m0 += UPD_TILE) {
             const int mt = min(UPD_TILE, u.n_moved - m0);
             for (int64_t p = pb + threadIdx.x; p < pe; p += UPD_HEAVY_THREADS) {
@@ -391,20 +438,23 @@ __global__ void __launch_bounds__(UPD_HEAVY_THREADS) k_upd_heavy(UpdateArgs u) {
                 const int mm = touched[e];
                 const unsigned long long S = acc[mm];
                 acc[mm] = 0ull;
-                update_entry<WRITE>(u, t, m0 + mm, S);
+                update_entry<WRITE>(u, t, m0 + mm, S, agg);
             }
             __syncthreads();
             if (threadIdx.x == 0) n_touched = 0;
             __syncthreads();
         }
     }
+    __syncthreads();
+    update_flush<WRITE>(u, agg);
 }
 
 static cudaError_t launch_update(const UpdateArgs &u, bool write, cudaStream_t st) {
     if (u.n_moved <= 0) return cudaSuccess;
     cudaError_t e;
-    const size_t smem_l = (size_t)UPD_SLOTS * (sizeof(unsigned long long) + sizeof(uint32_t));
-    const size_t smem_h = (size_t)UPD_TILE * (sizeof(unsigned long long) + sizeof(int32_t));
+    const size_t agg_bytes = (size_t)2 * UPD_AGG * sizeof(unsigned long long);
+    const size_t smem_l = (size_t)UPD_SLOTS * (sizeof(unsigned long long) + sizeof(uint32_t)) + agg_bytes;
+    const size_t smem_h = (size_t)UPD_TILE * (sizeof(unsigned long long) + sizeof(int32_t)) + agg_bytes;
     if (u.n_light > 0) {
         const int grid = min(u.n_light, 152 * 2 * 8);
         if (write) {

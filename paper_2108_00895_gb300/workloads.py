@@ -27,6 +27,7 @@ class Workload:
     prune: str              # "none" or "ncc"
     stop_on_no_change: bool
     seed_id: int
+    shift_tol: float = -1.0     # Sec. 4.1 stop rule (max squared centroid shift); < 0: off
 
     @property
     def corpus_seed(self) -> int:
@@ -54,6 +55,7 @@ class Workload:
                 "terms": f"Zipf(s={self.zipf_s:g}) without replacement",
                 "values": "(Poisson(1)+1)*ln(N/df), L2-normalised",
                 "precision": self.precision, "prune": self.prune, "max_iter": self.max_iter,
+                "shift_tol": self.shift_tol,
                 "seeds": {"corpus": self.corpus_seed, "init": self.init_seed}}
 
 
@@ -67,7 +69,16 @@ MEDIUM = Workload("ncc-fp32 N=300000 d=100000 k=1000", 300_000, 100_000, 1000, 1
 LARGE = Workload("ncc-bf16 N=2000000 d=250000 k=10000", 2_000_000, 250_000, 10_000, 150.0, 5, 2000,
                  1.05, 30, "bf16", "ncc", True, 3)
 
-ALL = {"small": SMALL, "medium": MEDIUM, "large": LARGE}
+# Analogs of the paper's two collections (Sec. 4.1): 1M tweets (783,304 terms, 10 nonzeros
+# on average) and 200k abstracts (325,556 terms, 58 on average), clustered with the paper's
+# stop rule (no assignment change or max squared centroid shift < 1e-4) at k = 50, 500 or
+# 5000 (Table 1). FP32 centroids with FP64 rescoring: exact, like the paper's CPU method.
+TWEETS = Workload("tweets-like N=1000000 d=783304 k=5000", 1_000_000, 783_304, 5000, 10.0, 2, 60, 1.05,
+                  200, "fp32", "ncc", True, 6, 1e-4)
+ABSTRACTS = Workload("abstracts-like N=200000 d=325556 k=5000", 200_000, 325_556, 5000, 58.0, 5, 600, 1.05,
+                     200, "fp32", "ncc", True, 7, 1e-4)
+
+ALL = {"small": SMALL, "medium": MEDIUM, "large": LARGE, "tweets": TWEETS, "abstracts": ABSTRACTS}
 
 
 @dataclass(frozen=True)
