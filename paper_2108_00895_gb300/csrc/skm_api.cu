@@ -79,6 +79,15 @@ struct skm_ctx {
     int64_t rare_c_rows = 0, rare_c_entries = 0;
     std::vector<uint32_t> h_rtot;
 
+    // support of each centroid column, known on the host (fit only): 0 = the terms of its
+    // current members, 1 = the terms of its seed document, 2 = unknown (cleared densely)
+    std::vector<uint8_t> csupport;
+    std::vector<uint8_t> h_changed;
+    std::vector<int32_t> h_sizes, h_list;
+    std::vector<uint8_t> h_flag;
+    Buf zflag, zlist;
+    bool cm_valid = false;   // the compacted moved matrix matches the last moved list
+
     skm_stats stats{};
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_score, ev_decide, ev_update, ev_index;
     std::vector<cudaEvent_t> ev_pool;
@@ -715,9 +724,79 @@ skm_status rescore_queues(skm_ctx *ctx, const DevCsr &dc, int32_t *a_new, float 
 
 // One update step: changed flags, moved list, the two posting passes, objective and shift.
 // Returns the number of documents whose assignment changed and |M| through the counters.
+// Clears the columns of the clusters recomputed by this update (changed, with members)
+// before the write pass. Inside a fit the host knows each column's support (csupport), so
+// only its nonzeros are cleared, unless clearing whole columns is cheaper; outside a fit
+// (and for unknown supports) whole columns are cleared.
+skm_status clear_recomputed(skm_ctx *ctx, const DevCsr &dc, const Postings &pg, const int32_t *a_old, bool sparse) {
+    const int32_t k = ctx->cfg.k;
+    float *C32 = P<float>(ctx->C32);
+    __nv_bfloat16 *C16 = ctx->cfg.precision == SKM_BF16 ? P<__nv_bfloat16>(ctx->C16) : nullptr;
+    ctx->h_changed.resize(k);
+    ctx->h_sizes.resize(k);
+    SKM_CUDA(cudaMemcpyAsync(ctx->h_changed.data(), ctx->changed.p, k, cudaMemcpyDeviceToHost, ctx->st));
+    SKM_CUDA(cudaMemcpyAsync(ctx->h_sizes.data(), ctx->sizes.p, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, ctx->st));
+    SKM_TRY(sync(ctx));
+    if ((int32_t)ctx->csupport.size() != k) sparse = false;
+    // cost of the member-postings pass (read every posting, scatter a few stores) against
+    // clearing whole columns (d rows x recomputed columns x element bytes)
+    int64_t n_members = 0, n_rec = 0;
+    for (int32_t j = 0; j < k; ++j) {
+        if (!ctx->h_changed[j] || ctx->h_sizes[j] == 0) continue;
+        ++n_rec;
+        if (sparse && ctx->csupport[j] == 0) ++n_members;
+    }
+    const int64_t elt = C16 ? 6 : 4;
+    if (sparse && n_members > 0 && (int64_t)ctx->d * n_members * elt < 2 * 16 * dc.nnz) sparse = false;
+    ctx->h_flag.assign(k, 0);
+    std::vector<int32_t> seeds;
+    ctx->h_list.clear();
+    for (int32_t j = 0; j < k; ++j) {
+        if (!ctx->h_changed[j] || ctx->h_sizes[j] == 0) continue;
+        const uint8_t sup = sparse ? ctx->csupport[j] : 2;
+        if (sup == 0) ctx->h_flag[j] = 1;
+        else if (sup == 1) seeds.push_back(j);
+        else ctx->h_list.push_back(j);
+    }
+    SKM_TRY(ensure(ctx, ctx->zflag, (size_t)k));
+    SKM_TRY(ensure(ctx, ctx->zlist, sizeof(int32_t) * (size_t)k));
+    if (n_members > 0 && sparse) {
+        SKM_CUDA(cudaMemcpyAsync(ctx->zflag.p, ctx->h_flag.data(), k, cudaMemcpyHostToDevice, ctx->st));
+        SKM_CUDA(launch_zero_members(P<int32_t>(ctx->row_idx), P<int32_t>(ctx->pterm), dc.nnz, a_old,
+                                     P<uint8_t>(ctx->zflag), C32, C16, ctx->ldc, ctx->st));
+        ctx->stats.launches_total++;
+    }
+    if (!seeds.empty()) {
+        SKM_CUDA(cudaMemcpyAsync(ctx->zlist.p, seeds.data(), sizeof(int32_t) * seeds.size(), cudaMemcpyHostToDevice,
+                                 ctx->st));
+        SKM_CUDA(launch_zero_seeds(P<int32_t>(ctx->zlist), (int32_t)seeds.size(), P<int32_t>(ctx->init_ids),
+                                   dc.row_ptr, dc.col, C32, C16, ctx->ldc, ctx->st));
+        ctx->stats.launches_total++;
+        SKM_TRY(sync(ctx));   // zlist is reused below
+    }
+    if (!ctx->h_list.empty()) {
+        SKM_CUDA(cudaMemcpyAsync(ctx->zlist.p, ctx->h_list.data(), sizeof(int32_t) * ctx->h_list.size(),
+                                 cudaMemcpyHostToDevice, ctx->st));
+        SKM_CUDA(launch_zero_cols(P<int32_t>(ctx->zlist), (int32_t)ctx->h_list.size(), ctx->d, C32, C16, ctx->ldc,
+                                  ctx->st));
+        ctx->stats.launches_total++;
+    }
+    // supports after this update: recomputed -> its new members; a changed cluster left
+    // without members keeps its centroid, whose support its members no longer describe
+    if ((int32_t)ctx->csupport.size() == k) {
+        for (int32_t j = 0; j < k; ++j) {
+            if (!ctx->h_changed[j]) continue;
+            if (ctx->h_sizes[j] > 0) ctx->csupport[j] = 0;
+            else if (ctx->csupport[j] == 0) ctx->csupport[j] = 2;
+        }
+    }
+    SKM_TRY(sync(ctx));   // the host vectors must outlive the copies
+    return SKM_OK;
+}
+
 skm_status update_step(skm_ctx *ctx, const DevCsr &dc, const Postings &pg, const int32_t *a_new,
                        const int32_t *a_old, int64_t n_docs, bool first, bool converged_check,
-                       bool *converged, int iter) {
+                       bool *converged, int iter, bool in_fit) {
     const int32_t k = ctx->cfg.k;
     Timed tm(ctx, ctx->ev_update);
     SKM_CUDA(cudaMemsetAsync(ctx->changed.p, 0, k, ctx->st));
@@ -761,9 +840,15 @@ skm_status update_step(skm_ctx *ctx, const DevCsr &dc, const Postings &pg, const
         u.normsq128 = P<unsigned long long>(ctx->normsq128);
         u.sq128 = P<unsigned long long>(ctx->sq128);
         u.inv_norm = P<double>(ctx->inv_norm);
+        // the compacted moved matrix serves the next pruned pass; when more than half of the
+        // clusters moved and the matrix is large (over 2 GB), the next step scores every
+        // document in full instead
+        const int64_t cm_bytes = (int64_t)ctx->d * n_moved * (ctx->cfg.precision == SKM_BF16 ? 2 : 4);
+        const bool build_cm = in_fit && ctx->cfg.prune == SKM_PRUNE_NCC &&
+                              (n_moved <= k / 2 || cm_bytes <= (int64_t(2) << 30));
         u.C32 = P<float>(ctx->C32);
         u.C16 = ctx->cfg.precision == SKM_BF16 ? P<__nv_bfloat16>(ctx->C16) : nullptr;
-        u.CM = ctx->CM.p;
+        u.CM = build_cm ? ctx->CM.p : nullptr;
         u.precision = ctx->cfg.precision;
         u.ldc = ctx->ldc;
         SKM_CUDA(cudaMemsetAsync(u.normsq128, 0, 2 * sizeof(unsigned long long) * n_moved, ctx->st));
@@ -771,8 +856,11 @@ skm_status update_step(skm_ctx *ctx, const DevCsr &dc, const Postings &pg, const
         SKM_CUDA(launch_update_norm(u, ctx->st));
         SKM_CUDA(launch_from_u128(u.normsq128, nullptr, n_moved, pg.F, P<double>(ctx->normsq), P<double>(ctx->inv_norm),
                                   nullptr, ctx->st));
-        SKM_CUDA(launch_zero_moved(u.moved, P<int32_t>(ctx->sizes), n_moved, ctx->d, u.C32, u.C16, u.CM, u.precision,
-                                   u.ldc, ctx->st));
+        SKM_TRY(clear_recomputed(ctx, dc, pg, a_old, in_fit));
+        if (build_cm)
+            SKM_CUDA(launch_cm_moved(u.moved, P<int32_t>(ctx->sizes), n_moved, ctx->d, u.C32, u.CM, u.precision,
+                                     u.ldc, ctx->st));
+        ctx->cm_valid = build_cm;
         SKM_CUDA(launch_update_write(u, ctx->st));
         SKM_CUDA(launch_from_u128(nullptr, u.sq128, n_moved, pg.F, nullptr, nullptr, P<double>(ctx->newsq), ctx->st));
         ctx->stats.launches_total += 8;
@@ -925,6 +1013,8 @@ skm_status skm_fit(skm_ctx *ctx, const skm_csr *docs, const int32_t *init_doc_id
                                    ctx->ldc, P<double>(ctx->sq_store), ctx->st));
     ctx->stats.launches_total++;
     ctx->cent_epoch++;
+    ctx->csupport.assign(k, 1);   // every column is its seed document
+    ctx->cm_valid = false;
     SKM_TRY(reset_skipped(ctx));
     SKM_CUDA(cudaMemsetAsync(ctx->clean.p, 0, N, ctx->st));
     SKM_CUDA(cudaMemsetAsync(ctx->changed.p, 1, k, ctx->st));
@@ -943,7 +1033,8 @@ skm_status skm_fit(skm_ctx *ctx, const skm_csr *docs, const int32_t *init_doc_id
         SKM_TRY(reset_counters(ctx));
         int32_t n_pruned = 0, n_full = (int32_t)N;
         const int32_t *full_list = P<int32_t>(ctx->order);
-        if (prune && !first) {
+        // the pruned pass needs the compacted matrix of the last update's moved list
+        if (prune && !first && ctx->cm_valid) {
             PartitionArgs pa{};
             pa.n_docs = N;
             pa.order = P<int32_t>(ctx->order);
@@ -990,7 +1081,7 @@ skm_status skm_fit(skm_ctx *ctx, const skm_csr *docs, const int32_t *init_doc_id
         ctx->stats.bytes += 8 * (dc.nnz + nnz_refull) + 20 * (N + n_refull) + pg.d_eff * cols_needed * elt;
         SKM_TRY(rescore_queues(ctx, dc, a_new, nullptr));
         bool converged = false;
-        SKM_TRY(update_step(ctx, dc, pg, a_new, a_old, N, first, true, &converged, t - 1));
+        SKM_TRY(update_step(ctx, dc, pg, a_new, a_old, N, first, true, &converged, t - 1, true));
         n_moved_prev = ctx->h_counters[CNT_MOVED];
         cur ^= 1;
         if (converged) break;
@@ -1104,7 +1195,9 @@ skm_status skm_update(skm_ctx *ctx, const skm_csr *docs, const int32_t *assign, 
     SKM_TRY(build_postings(ctx, dc, pg));
     SKM_TRY(reset_counters(ctx));
     bool conv = false;
-    SKM_TRY(update_step(ctx, dc, pg, a_dev, nullptr, N, true, false, &conv, 0));
+    ctx->csupport.clear();   // supports are tracked within a fit only
+    ctx->cm_valid = false;
+    SKM_TRY(update_step(ctx, dc, pg, a_dev, nullptr, N, true, false, &conv, 0, false));
     SKM_TRY(sync(ctx));
     collect_times(ctx);
     if (n_changed_out) *n_changed_out = ctx->h_counters[CNT_MOVED];
@@ -1126,6 +1219,8 @@ skm_status skm_set_centroids(skm_ctx *ctx, int32_t n_terms, const float *centroi
     }
     ctx->cent_epoch++;
     SKM_CUDA(launch_col_sq(P<float>(ctx->C32), ctx->ldc, n_terms, k, P<double>(ctx->sq_store), ctx->st));
+    ctx->csupport.clear();
+    ctx->cm_valid = false;
     return sync(ctx);
 }
 

@@ -152,7 +152,7 @@ struct UpdateArgs {
     const double *inv_norm;    // [n_moved]
     float *C32;
     __nv_bfloat16 *C16;        // nullable (FP32 mode)
-    void *CM;                  // compacted moved matrix (precision of the scored copy)
+    void *CM;                  // nullable: compacted moved matrix (precision of the scored copy)
     int precision;
     int64_t ldc;
 };
@@ -163,9 +163,17 @@ int update_chunk_postings();   // most postings of a light chunk
 cudaError_t launch_from_u128(const unsigned long long *normsq128, const unsigned long long *sq128, int32_t n,
                              int F, double *normsq, double *inv_norm, double *newsq, cudaStream_t st);
 // Zero the recomputed moved columns and fill the compacted matrix (see update.cu).
-cudaError_t launch_zero_moved(const int32_t *moved, const int32_t *sizes, int32_t n_moved, int32_t d,
-                              float *C32, __nv_bfloat16 *C16, void *CM, int precision, int64_t ldc,
-                              cudaStream_t st);
+// Clearing recomputed columns before the write pass (see update.cu): by the postings of the
+// flagged clusters' old members, by the seed documents of listed clusters, or all rows of
+// listed columns; and the compacted moved matrix (cleared or kept-centroid columns).
+cudaError_t launch_zero_members(const int32_t *row_idx, const int32_t *pterm, int64_t nnz, const int32_t *a_old,
+                                const uint8_t *flag, float *C32, __nv_bfloat16 *C16, int64_t ldc, cudaStream_t st);
+cudaError_t launch_zero_seeds(const int32_t *list, int32_t n, const int32_t *init_ids, const int64_t *row_ptr,
+                              const int32_t *col, float *C32, __nv_bfloat16 *C16, int64_t ldc, cudaStream_t st);
+cudaError_t launch_zero_cols(const int32_t *list, int32_t n, int32_t d, float *C32, __nv_bfloat16 *C16, int64_t ldc,
+                             cudaStream_t st);
+cudaError_t launch_cm_moved(const int32_t *moved, const int32_t *sizes, int32_t n_moved, int32_t d, const float *C32,
+                            void *CM, int precision, int64_t ldc, cudaStream_t st);
 cudaError_t launch_mdoc(const int32_t *a, const int32_t *pos_in_m, int64_t n, int32_t *mdoc,
                         cudaStream_t st);
 // Per-document FP64 objective terms of moved clusters, summed per cluster in fixed point.

@@ -16,6 +16,8 @@
 // accumulates the squared norm of the stored FP32 column (for the next step's shift). The objective term
 // S_j . c_j(old) comes from per-document FP64 dots against the old master (k_doc_obj),
 // summed per cluster in fixed point, before the update overwrites it.
+#include <algorithm>
+
 #include "skm_device.cuh"
 #include "skm_kernels.cuh"
 
@@ -323,10 +325,12 @@ __device__ __forceinline__ void update_entry(const UpdateArgs &u, int32_t t, int
     const int64_t row = (int64_t)t * u.ldc;
     u.C32[row + j] = c;
     if (u.C16) u.C16[row + j] = __float2bfloat16_rn(c);
-    if (u.precision == 1)
-        reinterpret_cast<__nv_bfloat16 *>(u.CM)[row + m] = __float2bfloat16_rn(c);
-    else
-        reinterpret_cast<float *>(u.CM)[row + m] = c;
+    if (u.CM) {
+        if (u.precision == 1)
+            reinterpret_cast<__nv_bfloat16 *>(u.CM)[row + m] = __float2bfloat16_rn(c);
+        else
+            reinterpret_cast<float *>(u.CM)[row + m] = c;
+    }
     const double c2 = (double)c * (double)c;   // exact (24-bit mantissa squared)
     const unsigned long long q = (unsigned long long)__double2ull_rn(ldexp(c2, 62));
     atomic_add_u128(dst, q, 0ull);
@@ -512,26 +516,61 @@ cudaError_t launch_from_u128(const unsigned long long *normsq128, const unsigned
 }
 
 // ------------------------------------------------------------------------------------
-// Moved columns before the write pass: a recomputed cluster's column is zeroed in the FP32
-// master and the BF16 copy (the write pass then stores its nonzeros); every compacted
-// column gets zero, or for a cluster left without members (which keeps its centroid) a
-// copy of the kept centroid. Store-only, one thread per (row, moved entry).
+// Recomputed columns are cleared before the write pass stores their nonzeros. The support
+// of a column is known in three cases, so only its nonzeros are cleared:
+//   k_zero_members: a centroid last computed from its current members has nonzeros exactly
+//     at their terms: entries (t, a_old[i]) over the postings (i, t) of flagged clusters
+//     (repeated stores of zero are harmless);
+//   k_zero_seeds: a centroid that is still its seed document: that document's terms;
+//   k_zero_cols: any other column (a centroid kept while its cluster was empty): all rows.
 // ------------------------------------------------------------------------------------
-__global__ void k_zero_moved(const int32_t *moved, const int32_t *sizes, int32_t n_moved, int32_t d,
-                             float *C32, __nv_bfloat16 *C16, void *CM, int precision, int64_t ldc) {
+__global__ void k_zero_members(const int32_t *row_idx, const int32_t *pterm, int64_t nnz, const int32_t *a_old,
+                               const uint8_t *flag, float *C32, __nv_bfloat16 *C16, int64_t ldc) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t j = __ldg(a_old + __ldg(row_idx + p));
+        if (!__ldg(flag + j)) continue;
+        const int64_t e = (int64_t)__ldg(pterm + p) * ldc + j;
+        C32[e] = 0.f;
+        if (C16) C16[e] = __float2bfloat16_rn(0.f);
+    }
+}
+
+__global__ void k_zero_seeds(const int32_t *list, int32_t n, const int32_t *init_ids, const int64_t *row_ptr,
+                             const int32_t *col, float *C32, __nv_bfloat16 *C16, int64_t ldc) {
+    const int lane = threadIdx.x & 31;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= n) return;
+    const int32_t j = list[w];
+    const int32_t doc = init_ids[j];
+    for (int64_t p = row_ptr[doc] + lane; p < row_ptr[doc + 1]; p += 32) {
+        const int64_t e = (int64_t)col[p] * ldc + j;
+        C32[e] = 0.f;
+        if (C16) C16[e] = __float2bfloat16_rn(0.f);
+    }
+}
+
+__global__ void k_zero_cols(const int32_t *list, int32_t n, int32_t d, float *C32, __nv_bfloat16 *C16, int64_t ldc) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int32_t j = list[q];
+    for (int64_t t = blockIdx.y; t < d; t += gridDim.y) {
+        C32[t * ldc + j] = 0.f;
+        if (C16) C16[t * ldc + j] = __float2bfloat16_rn(0.f);
+    }
+}
+
+// The compacted moved matrix for the next pruned pass: column m of a recomputed cluster is
+// cleared (the write pass stores its nonzeros); a cluster left without members keeps its
+// centroid, which is copied. Store-only except for those copies; one thread per (row, m).
+__global__ void k_cm_moved(const int32_t *moved, const int32_t *sizes, int32_t n_moved, int32_t d, const float *C32,
+                           void *CM, int precision, int64_t ldc) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= n_moved) return;
     const int32_t j = __ldg(moved + m);
     const bool recomputed = __ldg(sizes + j) > 0;
     for (int64_t t = blockIdx.y; t < d; t += gridDim.y) {
         const int64_t row = t * ldc;
-        float cur = 0.f;
-        if (recomputed) {
-            C32[row + j] = 0.f;
-            if (C16) C16[row + j] = __float2bfloat16_rn(0.f);
-        } else {
-            cur = C32[row + j];
-        }
+        const float cur = recomputed ? 0.f : C32[row + j];
         if (precision == 1)
             reinterpret_cast<__nv_bfloat16 *>(CM)[row + m] = __float2bfloat16_rn(cur);
         else
@@ -539,13 +578,38 @@ __global__ void k_zero_moved(const int32_t *moved, const int32_t *sizes, int32_t
     }
 }
 
-cudaError_t launch_zero_moved(const int32_t *moved, const int32_t *sizes, int32_t n_moved, int32_t d,
-                              float *C32, __nv_bfloat16 *C16, void *CM, int precision, int64_t ldc,
-                              cudaStream_t st) {
+static unsigned rows_grid(int32_t d, unsigned bx) {
+    return (unsigned)min((int64_t)d, max((int64_t)1, (int64_t)152 * 64 / bx));
+}
+
+cudaError_t launch_zero_members(const int32_t *row_idx, const int32_t *pterm, int64_t nnz, const int32_t *a_old,
+                                const uint8_t *flag, float *C32, __nv_bfloat16 *C16, int64_t ldc, cudaStream_t st) {
+    if (nnz <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((nnz + 255) / 256, 152 * 16);
+    k_zero_members<<<(unsigned)blocks, 256, 0, st>>>(row_idx, pterm, nnz, a_old, flag, C32, C16, ldc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_seeds(const int32_t *list, int32_t n, const int32_t *init_ids, const int64_t *row_ptr,
+                              const int32_t *col, float *C32, __nv_bfloat16 *C16, int64_t ldc, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_zero_seeds<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(list, n, init_ids, row_ptr, col, C32, C16, ldc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_cols(const int32_t *list, int32_t n, int32_t d, float *C32, __nv_bfloat16 *C16, int64_t ldc,
+                             cudaStream_t st) {
+    if (n <= 0 || d <= 0) return cudaSuccess;
+    const unsigned bx = (unsigned)((n + 255) / 256);
+    k_zero_cols<<<dim3(bx, rows_grid(d, bx)), 256, 0, st>>>(list, n, d, C32, C16, ldc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cm_moved(const int32_t *moved, const int32_t *sizes, int32_t n_moved, int32_t d, const float *C32,
+                            void *CM, int precision, int64_t ldc, cudaStream_t st) {
     if (n_moved <= 0 || d <= 0) return cudaSuccess;
     const unsigned bx = (unsigned)((n_moved + 255) / 256);
-    const unsigned by = (unsigned)min((int64_t)d, max((int64_t)1, (int64_t)152 * 64 / bx));
-    k_zero_moved<<<dim3(bx, by), 256, 0, st>>>(moved, sizes, n_moved, d, C32, C16, CM, precision, ldc);
+    k_cm_moved<<<dim3(bx, rows_grid(d, bx)), 256, 0, st>>>(moved, sizes, n_moved, d, C32, CM, precision, ldc);
     return cudaGetLastError();
 }
 

@@ -230,6 +230,27 @@ def test_fit_pruned_equals_full_bit_for_bit(skm, precision):
     assert pr.stats["sims"] < full.stats["sims"]
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_fit_large_vocabulary_short_documents(skm, precision):
+    """Short documents over a large vocabulary (the tweets shape of Sec. 4.1): the update
+    clears only the nonzeros of recomputed columns (their members' or seed document's
+    terms), and steps with more than half of the clusters moved are scored in full. The
+    pruned fit must equal the full one and the oracle."""
+    w = workloads.TWEETS.scaled(n_docs=4000, n_terms=60000, k=160, max_iter=25, shift_tol=-1.0)
+    docs = w.corpus()
+    ids = w.init_ids()
+    ref = oracle.fit(docs, w.k, ids, w.max_iter)
+    full, Cf = _fit_both(skm, w, docs, ids, precision, "none", w.max_iter)
+    pr, Cp = _fit_both(skm, w, docs, ids, precision, "ncc", w.max_iter)
+    assert pr.iters == full.iters == ref.iters
+    np.testing.assert_array_equal(pr.assign, full.assign)
+    np.testing.assert_array_equal(Cp, Cf)
+    np.testing.assert_array_equal(pr.assign, ref.a)
+    np.testing.assert_allclose(pr.objective, ref.objective, rtol=OBJ_RTOL, atol=0)
+    assert np.abs(Cp - ref.C).max() < CENT_ATOL
+    assert pr.stats["docs_pruned"] > 0
+
+
 def test_fit_step_locked_against_oracle(skm):
     """Each step checked on its own: the oracle's update of the GPU assignment gives the GPU
     centroids, and the oracle's assignment with the GPU centroids gives the GPU assignment."""
