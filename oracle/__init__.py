@@ -15,6 +15,7 @@ Spherical k-Means for Document Clustering" (DocEng 2021):
   and the dot product indexing structure (Sec. 3.2) as modes, and the stop rule of
   Sec. 4.1.
 * ``min_overlaps``, ``index_candidates``: the threshold index of Sec. 3.2 (Lemma 3.1).
+* ``kmeanspp``: k-means++ seeding, the initial assignment Sec. 2 names.
 
 The arithmetic lives in ``skm_oracle.c`` (plain C, IEEE double, no FMA contraction).
 """
@@ -73,6 +74,7 @@ def _load():
                 "oracle_index_candidates": (_I64, [_I64, _P, _P, _I32, _I32, _P, _D, _P, _P, _I64]),
                 "oracle_fit": (_I32, [_I64, _P, _P, _P, _I32, _I32, _P, _I32, _D, _INT, _INT, _P,
                                       _I32, _P, _P, _P, _P, _P]),
+                "oracle_kmeanspp": (_INT, [_I64, _P, _P, _P, _I32, _I32, _P, _P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -245,3 +247,17 @@ def fit(docs, k: int, init_ids: np.ndarray, max_iter: int, shift_tol: float = -1
     if it < 0:
         raise MemoryError("oracle_fit: allocation failed")
     return FitResult(C, a, int(it), obj[:it].copy(), nch[:it].copy(), sims[:it].copy())
+
+
+def kmeanspp(docs, k: int, uniforms: np.ndarray) -> np.ndarray:
+    """k-means++ seeds (Sec. 2's named initialisation; readings K1-K2 in skm_oracle.c):
+    document ids drawn with probability proportional to 1 - max over seeds of x . seed,
+    using the given uniforms in [0, 1)."""
+    rp, ci, va = _csr_args(docs)
+    u = np.ascontiguousarray(uniforms, dtype=np.float64)
+    if u.shape[0] < k:
+        raise ValueError("need k uniforms")
+    ids = np.empty(k, np.int32)
+    if _load().oracle_kmeanspp(docs.n_docs, _ptr(rp), _ptr(ci), _ptr(va), docs.n_terms, int(k), _ptr(u), _ptr(ids)) != 0:
+        raise MemoryError("oracle_kmeanspp: allocation failed")
+    return ids

@@ -282,3 +282,61 @@ def test_centroids_subset_matches_full_update():
     full = oracle.update(docs, a, np.zeros((docs.n_terms, k))).C
     sel = np.array([3, 0, 7])
     np.testing.assert_array_equal(oracle.centroids_subset(docs, a, sel), full[:, sel])
+
+
+# ---------------------------------------------------------------- k-means++ seeding (Sec. 2)
+def _docs_from_golden(g):
+    d = g["docs"]
+    return synth.Csr(np.array(d["row_ptr"], np.int64), np.array(d["col_idx"], np.int32),
+                     np.array(d["values"], np.float32), d["n_terms"])
+
+
+def test_hand_kmeanspp():
+    g = json.load(open(os.path.join(GOLD, "hand_kmeanspp.json")))
+    docs = _docs_from_golden(g)
+    for case in g["cases"]:
+        ids = oracle.kmeanspp(docs, len(case["ids"]), np.array(case["uniforms"]))
+        assert list(ids) == case["ids"]
+
+
+def test_kmeanspp_first_seed_and_only_weighted_document():
+    """Seed 0 is floor(u0 N). With 30 copies of one document and one orthogonal document,
+    after a copy is drawn the orthogonal document is the only one with positive weight, so
+    it is drawn whatever u1 is; then every weight is zero and the smallest undrawn
+    document follows."""
+    rows = [([0, 1], [0.6, 0.8])] * 30 + [([2], [1.0])]
+    docs = _csr_from_lists(rows, 3)
+    for u1 in (0.0, 0.37, 0.999):
+        ids = oracle.kmeanspp(docs, 3, np.array([0.5, u1, 0.5]))
+        assert ids[0] == 15 and ids[1] == 30 and ids[2] == 0
+
+
+def test_kmeanspp_draws_in_proportion_to_distance():
+    """Over evenly spaced u1, seed 1 lands on each document in proportion to
+    1 - x . seed0 (D^2 sampling for unit vectors), computed here from a dense copy."""
+    docs, _, _ = _tiny(41, n=60, d=120, k=2)
+    X = np.zeros((docs.n_docs, docs.n_terms))
+    for i in range(docs.n_docs):
+        a, b = docs.row_ptr[i], docs.row_ptr[i + 1]
+        X[i, docs.col_idx[a:b]] = docs.values[a:b]
+    u0 = 0.25
+    s0 = int(np.floor(u0 * docs.n_docs))
+    dist = np.maximum(1.0 - X @ X[s0], 0.0)
+    dist[s0] = 0.0
+    w = np.floor(dist * 2.0 ** 32)
+    Q = 20000
+    counts = np.zeros(docs.n_docs)
+    for q in range(Q):
+        ids = oracle.kmeanspp(docs, 2, np.array([u0, (q + 0.5) / Q]))
+        assert ids[0] == s0
+        counts[ids[1]] += 1
+    expect = Q * w / w.sum()
+    assert np.all(np.abs(counts - expect) <= 1.0 + 1e-9)
+
+
+def test_kmeanspp_seeds_are_distinct():
+    docs, _, _ = _tiny(43, n=200, d=300, k=50)
+    u = synth.uniform(17, 1, 50)
+    ids = oracle.kmeanspp(docs, 50, u)
+    assert len(set(ids.tolist())) == 50
+    assert ids.min() >= 0 and ids.max() < docs.n_docs
