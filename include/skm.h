@@ -169,6 +169,26 @@ SKM_API skm_status skm_assign(skm_ctx *ctx, const skm_csr *docs, int32_t *assign
 SKM_API skm_status skm_update(skm_ctx *ctx, const skm_csr *docs, const int32_t *assign,
                       int32_t *n_changed_out);
 
+/* k-means++ seeding of k = skm_config.k initial documents for skm_fit (Sec. 2 names the
+ * k-Means++ strategy as the usual initial assignment). Each seed is drawn with probability
+ * proportional to the squared distance to the nearest seed drawn so far, which for unit
+ * vectors is 2 (1 - x . seed):
+ *   seed 0 is document floor(uniforms[0] * n_docs);
+ *   seed r >= 1 is the smallest document whose inclusive prefix sum (document order) of the
+ *   integer weights w_i = floor(max(1 - max over seeds of x_i . seed, 0) * 2^32) (0 for
+ *   documents already drawn) exceeds min(floor(uniforms[r] * W), W - 1), W = sum of the
+ *   weights; when W = 0 it is the smallest document not drawn yet.
+ * The distances are computed in float, 1 - x . seed with one fused multiply-add per nonzero
+ * of the document in CSR order, so the seeds depend only on the documents and the uniforms.
+ * docs:      as for skm_fit (validated, staged when on the host).
+ * uniforms:  k host doubles in [0, 1), the procedure's random numbers (caller-owned).
+ * ids_out:   k int32 document ids (distinct): device memory if docs->on_device, host otherwise.
+ * Errors: SKM_ERR_INVALID (a uniform outside [0, 1), k > n_docs, NULL buffers or invalid
+ * documents), SKM_ERR_OOM / SKM_ERR_BUDGET (work buffers: 13 bytes per document, 4 per
+ * term), SKM_ERR_CUDA. */
+SKM_API skm_status skm_init_kmeanspp(skm_ctx *ctx, const skm_csr *docs, const double *uniforms,
+                                     int32_t *ids_out);
+
 /* Replace the resident centroids with a host or device float[n_terms * k] matrix
  * (term-major). The lower-precision copy is re-derived (round to nearest even). */
 SKM_API skm_status skm_set_centroids(skm_ctx *ctx, int32_t n_terms, const float *centroids,

@@ -87,6 +87,8 @@ struct skm_ctx {
     std::vector<uint8_t> h_flag;
     Buf zflag, zlist;
     bool cm_valid = false;   // the compacted moved matrix matches the last moved list
+    // k-means++ seeding
+    Buf pp_dist, pp_w, pp_csum, pp_drawn, pp_seed, pp_ids, pp_u;
 
     skm_stats stats{};
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_score, ev_decide, ev_update, ev_index;
@@ -944,7 +946,8 @@ skm_status skm_destroy(skm_ctx *ctx) {
                   &ctx->cand_cnt, &ctx->changed, &ctx->sizes, &ctx->moved,
                   &ctx->pos_in_m, &ctx->normsq, &ctx->inv_norm, &ctx->dot_fx, &ctx->newsq,
                   &ctx->rflag, &ctx->rtot, &ctx->rbase, &ctx->rptr_c, &ctx->rent_c, &ctx->rptr_m, &ctx->rent_m,
-                  &ctx->colm, &ctx->skipped,
+                  &ctx->colm, &ctx->skipped, &ctx->zflag, &ctx->zlist, &ctx->pp_dist, &ctx->pp_w, &ctx->pp_csum,
+                  &ctx->pp_drawn, &ctx->pp_seed, &ctx->pp_ids, &ctx->pp_u,
                   &ctx->normsq128, &ctx->sq128, &ctx->sq_store, &ctx->counters, &ctx->counters64, &ctx->scal,
                   &ctx->obj, &ctx->init_ids};
     for (Buf *b : all) release(ctx, *b);
@@ -957,6 +960,51 @@ skm_status skm_destroy(skm_ctx *ctx) {
 }
 
 const char *skm_last_error(const skm_ctx *ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
+
+skm_status skm_init_kmeanspp(skm_ctx *ctx, const skm_csr *docs, const double *uniforms, int32_t *ids_out) {
+    SKM_TRY(common_checks(ctx));
+    DeviceGuard g(ctx->cfg.device);
+    const int32_t k = ctx->cfg.k;
+    if (!uniforms || !ids_out) return fail(ctx, SKM_ERR_INVALID, "uniforms and ids_out are required");
+    for (int32_t j = 0; j < k; ++j)
+        if (!(uniforms[j] >= 0.0 && uniforms[j] < 1.0))
+            return fail(ctx, SKM_ERR_INVALID, "uniforms[%d] = %g is outside [0, 1)", j, uniforms[j]);
+    if (docs && docs->n_docs < k)
+        return fail(ctx, SKM_ERR_INVALID, "k = %d exceeds n_docs = %lld", k, (long long)docs->n_docs);
+    DevCsr dc{};
+    SKM_TRY(stage_docs(ctx, docs, dc));
+    const int64_t n = dc.n;
+    SKM_TRY(ensure(ctx, ctx->pp_dist, sizeof(float) * n));
+    SKM_TRY(ensure(ctx, ctx->pp_w, sizeof(unsigned long long) * n));
+    SKM_TRY(ensure(ctx, ctx->pp_csum, sizeof(unsigned long long) * kmeanspp_chunks(n)));
+    SKM_TRY(ensure(ctx, ctx->pp_drawn, (size_t)n));
+    SKM_TRY(ensure(ctx, ctx->pp_seed, sizeof(float) * dc.d));
+    SKM_TRY(ensure(ctx, ctx->pp_ids, sizeof(int32_t) * k));
+    SKM_TRY(ensure(ctx, ctx->pp_u, sizeof(double) * k));
+    SKM_TRY(ensure_doc_bufs(ctx, n));
+    // seed 0 = floor(u_0 N)
+    int32_t first = (int32_t)std::floor(uniforms[0] * (double)n);
+    if (first >= n) first = (int32_t)(n - 1);
+    const uint8_t one = 1;
+    SKM_CUDA(cudaMemsetAsync(ctx->pp_drawn.p, 0, (size_t)n, ctx->st));
+    SKM_CUDA(cudaMemsetAsync(ctx->pp_seed.p, 0, sizeof(float) * dc.d, ctx->st));
+    SKM_CUDA(cudaMemcpyAsync(P<uint8_t>(ctx->pp_drawn) + first, &one, 1, cudaMemcpyHostToDevice, ctx->st));
+    SKM_CUDA(cudaMemcpyAsync(ctx->pp_ids.p, &first, sizeof(int32_t), cudaMemcpyHostToDevice, ctx->st));
+    SKM_CUDA(cudaMemcpyAsync(ctx->pp_u.p, uniforms, sizeof(double) * k, cudaMemcpyHostToDevice, ctx->st));
+    SKM_CUDA(launch_order_by_length(dc.row_ptr, n, P<int32_t>(ctx->order_hist), P<int32_t>(ctx->order), ctx->st));
+    SKM_CUDA(launch_kmeanspp(n, dc.d, k, P<int32_t>(ctx->order), dc.row_ptr, dc.col, dc.val, P<double>(ctx->pp_u),
+                             P<int32_t>(ctx->pp_ids), P<float>(ctx->pp_dist), P<unsigned long long>(ctx->pp_w),
+                             P<unsigned long long>(ctx->pp_csum), P<uint8_t>(ctx->pp_drawn), P<float>(ctx->pp_seed),
+                             ctx->st));
+    std::vector<int32_t> ids(k);
+    SKM_CUDA(cudaMemcpyAsync(ids.data(), ctx->pp_ids.p, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, ctx->st));
+    SKM_TRY(sync(ctx));
+    for (int32_t j = 0; j < k; ++j)
+        if (ids[j] < 0 || ids[j] >= n) return fail(ctx, SKM_ERR_CUDA, "k-means++ seed %d out of range", j);
+    SKM_CUDA(cudaMemcpyAsync(ids_out, ids.data(), sizeof(int32_t) * k,
+                             docs->on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, ctx->st));
+    return sync(ctx);
+}
 
 skm_status skm_prepare_assign(skm_ctx *ctx) {
     if (!ctx) return SKM_ERR_INVALID;

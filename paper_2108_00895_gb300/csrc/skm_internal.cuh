@@ -145,4 +145,13 @@ cudaError_t launch_rare_fill(const void *M, int precision, int64_t ldc, int32_t 
                              void *ent, cudaStream_t st);
 cudaError_t launch_mark_rare(const int32_t *col, int64_t nnz, const uint8_t *flag, int32_t *colm, cudaStream_t st);
 
+// k-means++ seeding (defined in init.cu): rounds 1..k-1 given ids[0] on the device, drawn
+// (n bytes) zero except drawn[ids[0]] = 1 and seed (d floats) zero; u: k uniforms on the
+// device; dist, w: n entries; csum: kmeanspp_chunks(n) entries. Leaves seed zero.
+cudaError_t launch_kmeanspp(int64_t n, int32_t d, int32_t k, const int32_t *order, const int64_t *row_ptr,
+                            const int32_t *col, const float *val, const double *u, int32_t *ids, float *dist,
+                            unsigned long long *w, unsigned long long *csum, uint8_t *drawn, float *seed,
+                            cudaStream_t st);
+int kmeanspp_chunks(int64_t n);
+
 }  // namespace skm

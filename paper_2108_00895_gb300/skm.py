@@ -121,7 +121,7 @@ EXPORTS = ("skm_config_default", "skm_create", "skm_destroy", "skm_last_error", 
            "skm_assign", "skm_update", "skm_set_centroids", "skm_get_centroids", "skm_n_terms",
            "skm_get_stats", "skm_mem_used", "skm_fit_batched", "skm_server_create", "skm_server_submit_assign",
            "skm_server_submit_fit", "skm_server_wait", "skm_server_release", "skm_server_get_stats",
-           "skm_server_destroy", "skm_assign_fixed_scratch")
+           "skm_server_destroy", "skm_assign_fixed_scratch", "skm_init_kmeanspp")
 
 # skm_assign_fixed_scratch: capacity of its fixed scratch, in (document x 256-column slice) units
 FIXED_SCRATCH_SLICE = 256
@@ -150,6 +150,7 @@ def load(build_if_missing: bool = True):
             "skm_fit": (st, [P, ctypes.POINTER(skm_csr), P, P, P, P]),
             "skm_assign": (st, [P, ctypes.POINTER(skm_csr), P, P]),
             "skm_update": (st, [P, ctypes.POINTER(skm_csr), P, P]),
+            "skm_init_kmeanspp": (st, [P, ctypes.POINTER(skm_csr), P, P]),
             "skm_set_centroids": (st, [P, ctypes.c_int32, P, ctypes.c_int32]),
             "skm_get_centroids": (st, [P, P, ctypes.c_int32]),
             "skm_n_terms": (ctypes.c_int32, [P]),
@@ -256,6 +257,10 @@ def skm_fit(ctx, csr: skm_csr, init_ids, assign_out, objective_out=None, iters_o
     if iters_out is not None:
         iters_out[0] = it.value
     return it.value
+
+
+def skm_init_kmeanspp(ctx, csr: skm_csr, uniforms, ids_out) -> None:
+    _check(ctx, load().skm_init_kmeanspp(ctx, ctypes.byref(csr), _ptr(uniforms), _ptr(ids_out)))
 
 
 def skm_assign(ctx, csr: skm_csr, assign_out, score_out=None) -> None:
@@ -441,6 +446,21 @@ class SphericalKMeans:
         obj = np.zeros(self.max_iter, np.float64)
         it = skm_fit(self.ctx, csr, ids, assign_out, obj)
         return FitResult(assign_out, obj[:it].copy(), it, skm_get_stats(self.ctx).as_dict())
+
+    def init_kmeanspp(self, docs, uniforms, n_terms: int | None = None) -> np.ndarray:
+        """k-means++ seeds (k document ids) drawn with the given k uniforms in [0, 1)."""
+        csr, keep, on_dev = make_csr(docs, n_terms)
+        u = np.ascontiguousarray(uniforms, dtype=np.float64)
+        if u.shape[0] < self.k:
+            raise ValueError("need k uniforms")
+        if on_dev:
+            import torch
+            ids = torch.empty(self.k, dtype=torch.int32, device=keep[0].device)
+            skm_init_kmeanspp(self.ctx, csr, u, ids)
+            return ids.cpu().numpy()
+        ids = np.empty(self.k, np.int32)
+        skm_init_kmeanspp(self.ctx, csr, u, ids)
+        return ids
 
     def assign(self, docs, n_terms: int | None = None, assign_out=None, score_out=None,
                want_scores: bool = True):
