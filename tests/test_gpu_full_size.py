@@ -1,0 +1,105 @@
+"""Parity at the benchmark's full sizes, in the configuration bench.py times.
+
+The oracle cannot run these fits end to end. Two approaches cover them:
+- Step-locked checks: fit T-1 steps for C_{T-1}, then the same T-step fit (deterministic)
+  for a_T, C_T and the objective. Then compare on 2,000 sampled documents: a_T against the
+  oracle's argmax over C_{T-1}, the sampled columns of C_T against the oracle's update from
+  a_T, and the objective against the oracle's sum over all documents.
+- Properties that hold at any size: the pruned fit equals the full fit bit for bit.
+
+Tolerances as in test_gpu_parity: assignments exact where the oracle's top-2 margin is at
+least 1e-5, centroids 1e-5 max-abs (FP32 master), objective 1e-6 relative.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2108_00895_gb300 import synth, workloads
+
+pytestmark = pytest.mark.gpu
+
+MARGIN = 1e-5
+OBJ_RTOL = 1e-6
+CENT_ATOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def skm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2108_00895_gb300 import skm as mod
+    mod.load()
+    return mod
+
+
+def _device(docs):
+    import torch
+    return (torch.from_numpy(docs.row_ptr).cuda(), torch.from_numpy(docs.col_idx).cuda(),
+            torch.from_numpy(docs.values).cuda())
+
+
+def _fit(skm, w, dev, n_terms, ids, max_iter, prune=None):
+    import torch
+    with skm.SphericalKMeans(w.k, precision=w.precision, prune=prune or w.prune, max_iter=max_iter,
+                             shift_tol=w.shift_tol, tau=1e-4) as km:
+        r = km.fit(dev, ids, n_terms=n_terms)
+        C = km.centroids()
+    torch.cuda.synchronize()
+    a = r.assign.cpu().numpy() if hasattr(r.assign, "cpu") else np.asarray(r.assign)
+    return a, r, C
+
+
+def _step_locked(skm, w, T, n_sample, n_clusters):
+    docs = w.corpus()
+    ids = w.init_ids()
+    dev = _device(docs)
+    _, _, C_prev = _fit(skm, w, dev, docs.n_terms, ids, T - 1)
+    a, r, C = _fit(skm, w, dev, docs.n_terms, ids, T)
+    assert r.iters == T
+    # assignments of sampled documents against the centroids they were scored on
+    sample = synth.sample_ids(docs.n_docs, n_sample, 31)
+    a_or, s1, s2 = oracle.assign(docs.rows(sample), C_prev)
+    clear = (s1 - s2) >= MARGIN
+    bad = np.nonzero((a[sample] != a_or) & clear)[0]
+    assert len(bad) == 0, f"{len(bad)} clear-margin mismatches of {len(sample)}"
+    assert clear.mean() > 0.5
+    # the step's objective over all documents: sum_i x_i . c_{a_i} with the scored centroids
+    obj = oracle.objective(docs, C_prev, a)
+    assert abs(r.objective[-1] - obj) <= OBJ_RTOL * abs(obj)
+    # sampled centroid columns: the normalised sums of their members under a_T
+    sizes = np.bincount(a, minlength=w.k)
+    populated = np.nonzero(sizes > 0)[0]
+    cl = populated[synth.sample_ids(len(populated), n_clusters, 32)]
+    ref = oracle.centroids_subset(docs, a, cl)
+    assert np.abs(C[:, cl] - ref).max() < CENT_ATOL
+
+
+def test_large_workload_step_locked(skm):
+    """N = 2M, d = 250k, k = 10,000, BF16 centroids, NCC, FP64 rescoring."""
+    _step_locked(skm, workloads.LARGE, 3, 2000, 40)
+
+
+def test_medium_workload_step_locked(skm):
+    """N = 300k, d = 100k, k = 1,000, FP32 centroids, NCC."""
+    _step_locked(skm, workloads.MEDIUM, 12, 2000, 40)
+
+
+@pytest.mark.parametrize("name", ["medium", "tweets"])
+def test_pruned_equals_full_at_full_size(skm, name):
+    """Sec. 3.1 is exact: the NCC fit and the full fit agree bit for bit, at the medium
+    workload (50 steps) and the tweets-like analog (N = 1M, d = 783,304, k = 500, the
+    paper's stop rule; k = 500 keeps the compared centroid matrices at 1.6 GB)."""
+    w = workloads.ALL[name]
+    if name == "tweets":
+        w = w.scaled(k=500)
+    docs = w.corpus()
+    ids = w.init_ids()
+    dev = _device(docs)
+    a_n, r_n, C_n = _fit(skm, w, dev, docs.n_terms, ids, w.max_iter, prune="ncc")
+    a_f, r_f, C_f = _fit(skm, w, dev, docs.n_terms, ids, w.max_iter, prune="none")
+    assert r_n.iters == r_f.iters
+    np.testing.assert_array_equal(a_n, a_f)
+    np.testing.assert_array_equal(r_n.objective, r_f.objective)
+    np.testing.assert_array_equal(C_n, C_f)
+    assert r_n.stats["docs_pruned"] > 0
