@@ -36,6 +36,13 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
+# DRAM bytes (read + write) of one k_score launch of the large workload's first step (a
+# full pass: 2M documents x 10,000 centroids, 325 ms), from one ncu capture recorded in
+# profiles/k_score_traffic_large_full_pass.md; it is reported for the default large
+# workload only and must be retaken whenever k_score changes.
+LARGE_FULL_PASS_TRAFFIC = 951.08e9 + 1.29e9
+LARGE_FULL_PASS_ALG_BYTES = 7.43e9
+
 METRIC = "docs assigned/s per iteration"
 UNIT = "docs/s"
 FP32_LANES_PER_SM = 128
@@ -226,6 +233,11 @@ def run_reference(args, w, world, rank, dist):
     print(json.dumps(line), flush=True)
 
 
+def workloads_large_name() -> str:
+    from paper_2108_00895_gb300 import workloads
+    return workloads.LARGE.name
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args, w, world, rank, local, dist):
     import torch
@@ -297,13 +309,17 @@ def run_ours(args, w, world, rank, local, dist):
 
     pk = peaks()
     fl = 2.0 * agg["fmas_exec"]          # multiply-adds the scoring passes executed
+    default_large = (w.name == workloads_large_name() and args.sparse_div == 0)
     score_s = agg["ms_score"] / 1e3
     achieved_tf = fl / score_s / 1e12 if score_s > 0 else None
     hbm_gbs = agg["bytes"] / score_s / 1e9 if score_s > 0 else None
     t_roof = max(agg["bytes"] / (pk["hbm_gbs"] * 1e9), fl / (pk["fp32_tflops"] * 1e12))
     roofline = {"bound": "alu", "achieved": achieved_tf, "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
                 "frac": achieved_tf / pk["fp32_tflops"] if achieved_tf else None,
-                "traffic": None,
+                "traffic": LARGE_FULL_PASS_TRAFFIC if default_large else None,
+                "traffic_scope": ("one full-pass k_score launch of step 1 (2M documents x 10,000 centroids); "
+                                  f"algorithmic bytes of that launch {LARGE_FULL_PASS_ALG_BYTES:.3g}")
+                if default_large else None,
                 "kernel": "k_score (scoring pass: fused CSR x term-major centroid SpMM + top-4)",
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)",
                 "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": pk["hbm_gbs"],
