@@ -13,7 +13,7 @@ Metric: documents assigned per second per iteration (N x iterations / time).
   python bench.py --impl reference ...   (the FP64 CPU oracle on host cores)
 
 Variants of a fit workload for comparisons and profiling (the JSON config records them):
-  --precision bf16|fp32  --prune ncc|none  --rescore on|off  --max-iter N
+  --precision bf16|fp32  --prune ncc|none|ncc_index  --rescore on|off  --max-iter N
   --sparse-div D (sparse centroid rows)  --case N,D,K (documents, vocabulary, clusters)  --k K
 
 Under torchrun (N > 1) each rank runs an independent replica (different seeds) on its
@@ -257,7 +257,8 @@ def run_ours(args, w, world, rank, local, dist):
     stream = torch.cuda.current_stream(dev)
     km = skm.SphericalKMeans(w.k, precision=w.precision, prune=w.prune, max_iter=w.max_iter,
                              shift_tol=w.shift_tol, rescore=args.rescore == "on", tau=args.tau, device=local,
-                             stream=stream.cuda_stream, timing=True, sparse_div=args.sparse_div)
+                             stream=stream.cuda_stream, timing=True, sparse_div=args.sparse_div,
+                             index_min_changed=args.index_min_changed, index_max_cands=args.index_max_cands)
     a_dev = torch.empty(N, dtype=torch.int32, device=dev)
     for _ in range(args.warmup):
         km.fit(d_docs, ids, n_terms=docs.n_terms, assign_out=a_dev)
@@ -273,7 +274,8 @@ def run_ours(args, w, world, rank, local, dist):
     iters = 0
     agg = {"fmas": 0, "fmas_exec": 0, "bytes": 0, "ms_score": 0.0, "ms_decide": 0.0, "ms_update": 0.0,
            "launches_total": 0, "launches_score": 0, "sims": 0, "docs_pruned": 0, "docs_full": 0,
-           "docs_rescored": 0, "docs_rescored_full": 0}
+           "docs_rescored": 0, "docs_rescored_full": 0, "index_docs": 0, "index_sims": 0, "index_entries": 0,
+           "index_products": 0, "ms_query": 0.0, "ms_index": 0.0}
     objectives = None
     for _ in range(args.steps):
         r = km.fit(d_docs, ids, n_terms=docs.n_terms, assign_out=a_dev)
@@ -348,7 +350,9 @@ def run_ours(args, w, world, rank, local, dist):
                                step="one full clustering job (fit)", iterations_per_step=iters / args.steps,
                                l2="inputs larger than L2 (CSR + centroid matrices >> 129 MB)",
                                objective_last=float(objectives[-1]) if objectives is not None else None,
-                               tau=args.tau, rescore=args.rescore, sparse_div=args.sparse_div),
+                               tau=args.tau, rescore=args.rescore, sparse_div=args.sparse_div,
+                               index_min_changed=args.index_min_changed if w.prune == "ncc_index" else None,
+                               index_max_cands=args.index_max_cands if w.prune == "ncc_index" else None),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": int(agg["launches_total"]),
                 "work": {k_: v for k_, v in agg.items()}}
@@ -559,7 +563,11 @@ def main():
     ap.add_argument("--profile-run", action="store_true",
                     help="allow fewer warm-up steps (launch lists under a profiler; not a timed number)")
     ap.add_argument("--precision", choices=["bf16", "fp32"], default=None, help="override the workload's")
-    ap.add_argument("--prune", choices=["ncc", "none"], default=None, help="override the workload's")
+    ap.add_argument("--prune", choices=["ncc", "none", "ncc_index"], default=None, help="override the workload's")
+    ap.add_argument("--index-min-changed", type=int, default=100,
+                    help="ncc_index: steps use the threshold index after more than this many centroids changed")
+    ap.add_argument("--index-max-cands", type=int, default=0,
+                    help="ncc_index: documents with more candidates are scored densely (0 = cost rule)")
     ap.add_argument("--rescore", choices=["on", "off"], default="on", help="FP64 rescoring of near ties")
     ap.add_argument("--max-iter", type=int, default=None, help="override the workload's step limit")
     ap.add_argument("--sparse-div", type=int, default=0, help="sparse centroid rows (0 = off)")

@@ -54,7 +54,8 @@ typedef enum {
 } skm_status;
 
 enum { SKM_FP32 = 0, SKM_BF16 = 1 };          /* centroid storage for the scoring pass */
-enum { SKM_PRUNE_NONE = 0, SKM_PRUNE_NCC = 1 }; /* Sec. 3.1 skip on or off */
+/* Sec. 3.1 skip off or on; NCC_INDEX adds the threshold index of Sec. 3.2 (skm_fit only) */
+enum { SKM_PRUNE_NONE = 0, SKM_PRUNE_NCC = 1, SKM_PRUNE_NCC_INDEX = 2 };
 
 /* Device memory provider. alloc returns NULL on failure; free receives the same size. */
 typedef void *(*skm_alloc_fn)(size_t bytes, void *user);
@@ -85,10 +86,29 @@ typedef struct {
                              pass reads those lists instead of the dense rows. Scores and
                              results are bit-identical either way. 0 = off (the default);
                              used for k >= 64 */
+    int32_t index_levels; /* SKM_PRUNE_NCC_INDEX: thresholds in index_lambda, 1..4 */
+    double index_lambda[4]; /* minimum dot products of the threshold indexes (Sec. 3.2),
+                               ascending, in (0, 1]; default 0.1, 0.25, 0.4, 0.6 (Sec. 4.1).
+                               A document whose similarity b to its previous centroid is at
+                               least lambda ||x|| for some level is scored only against the
+                               candidates of the highest such level (and, when its cluster
+                               did not change, only against changed ones, Sec. 3.1); every
+                               other centroid has similarity below lambda ||x|| <= b. Results
+                               are those of the unindexed loop. Used for k <= 16384, for
+                               documents of at most 64 nonzeros with at most
+                               index_max_cands candidates; the others are scored densely. */
+    int32_t index_min_changed; /* the index serves a step only when more than this many
+                                  centroids changed in the previous update (Sec. 4.3
+                                  suggests 100, the default); -1: every step after the first */
+    int32_t index_max_cands; /* a document with more candidates than this is scored densely:
+                                0 (the default) = min(512, k * (element bytes) / 32), where
+                                scoring the candidates one by one (a 32-byte sector per
+                                product) stops being cheaper than a dense pass; at most 512 */
 } skm_config;
 
 /* Fills a config with defaults: FP32, no pruning, max_iter 20, shift test off, rescoring
- * on with tau 0, no budget, device 0, default stream, cudaMalloc, sparse rows off. */
+ * on with tau 0, no budget, device 0, default stream, cudaMalloc, sparse rows off, the
+ * four index thresholds of Sec. 4.1 with index_min_changed 100. */
 SKM_API void skm_config_default(skm_config *cfg, int32_t k);
 
 typedef struct {
@@ -123,6 +143,12 @@ typedef struct {
     double ms_index;            /* device time building the sparse-row index */
     int64_t sparse_rows;        /* rows of the centroid matrix stored by their nonzeros */
     int64_t sparse_entries;     /* nonzeros stored for them */
+    int64_t index_docs;         /* document-steps decided through the threshold index */
+    int64_t index_sims;         /* similarities those computed (baseline + candidates, FP64) */
+    int64_t index_entries;      /* P_lambda entries they walked */
+    int64_t index_products;     /* (term, candidate) products they computed */
+    double ms_query;            /* device time in the index query kernel (ms_index also counts
+                                   the threshold index builds) */
 } skm_stats;
 
 /* Create a context on cfg->device. cfg is copied. */
@@ -188,6 +214,24 @@ SKM_API skm_status skm_update(skm_ctx *ctx, const skm_csr *docs, const int32_t *
  * term), SKM_ERR_CUDA. */
 SKM_API skm_status skm_init_kmeanspp(skm_ctx *ctx, const skm_csr *docs, const double *uniforms,
                                      int32_t *ids_out);
+
+/*
+ * Candidate sets of the threshold index (Sec. 3.2) of the resident centroids at threshold
+ * index_lambda[level], for checking the index: no baseline, no Sec. 3.1 filter.
+ * Centroid j is a candidate of document i when, for some term t of the document whose entry
+ * c_jt is in P_lambda with minimum overlap count m (a lower bound of the paper's count,
+ * clamped to 255), the document shares at least min(m, 255) terms with centroid j. Every
+ * centroid with x_i . c_j >= lambda ||x_i|| is a candidate (Lemma 3.1), and so is every
+ * candidate of the paper's exact construction. Documents with more than 64 nonzeros are
+ * not indexed (skm_fit scores them densely): every centroid is reported for them.
+ * docs:  as for skm_assign (n_terms = the resident vocabulary).
+ * bits:  host uint32[n_docs * ceil(k / 32)]; bit b of bits[i * ceil(k / 32) + w] is set when
+ *        centroid 32 w + b is a candidate of document i.
+ * Errors: SKM_ERR_STATE (no resident centroids), SKM_ERR_INVALID (level outside
+ * [0, index_levels), k > 16384, NULL bits, invalid documents), SKM_ERR_OOM / SKM_ERR_BUDGET
+ * (the index: 4 bytes per term per 32 centroids, 4 bytes per nonzero of the centroid matrix
+ * per level, 2.5 KB per centroid and 512 bytes per centroid per level), SKM_ERR_CUDA. */
+SKM_API skm_status skm_index_candidates(skm_ctx *ctx, const skm_csr *docs, int32_t level, uint32_t *bits);
 
 /* Replace the resident centroids with a host or device float[n_terms * k] matrix
  * (term-major). The lower-precision copy is re-derived (round to nearest even). */

@@ -89,9 +89,12 @@ struct skm_ctx {
     bool cm_valid = false;   // the compacted moved matrix matches the last moved list
     // k-means++ seeding
     Buf pp_dist, pp_w, pp_csum, pp_drawn, pp_seed, pp_ids, pp_u;
+    // threshold index of Sec. 3.2 (tindex.cu), built for centroid epoch ti_epoch
+    Buf ti_G, ti_gcnt, ti_gptr, ti_hist, ti_mtab, ti_P, ti_pbe, ti_stats, ti_dump;
+    int64_t ti_epoch = 0, ti_nzC = 0;
 
     skm_stats stats{};
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_score, ev_decide, ev_update, ev_index;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_score, ev_decide, ev_update, ev_index, ev_query;
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_next = 0;
 };
@@ -205,6 +208,7 @@ void collect_times(skm_ctx *ctx) {
     ctx->stats.ms_decide += sum(ctx->ev_decide);
     ctx->stats.ms_update += sum(ctx->ev_update);
     ctx->stats.ms_index += sum(ctx->ev_index);
+    ctx->stats.ms_query += sum(ctx->ev_query);
     ctx->ev_next = 0;
 }
 
@@ -570,6 +574,62 @@ const SparseArgs *apply_rare(skm_ctx *ctx, const RareView &rv, ScoreArgs &sa, Sp
 
 // Scoring pass over a document list (nullable = all) against all k or the moved list,
 // followed by the decision kernel.
+// Threshold index (Sec. 3.2) of the resident FP32 master, rebuilt when the centroids changed.
+skm_status build_tindex(skm_ctx *ctx) {
+    if (ctx->ti_epoch == ctx->cent_epoch) return SKM_OK;
+    const int32_t k = ctx->cfg.k, d = ctx->d, W = ti_words(k);
+    const int L = ctx->cfg.index_levels;
+    Timed tm(ctx, ctx->ev_index);
+    SKM_TRY(ensure(ctx, ctx->ti_G, sizeof(uint32_t) * (size_t)d * W));
+    SKM_TRY(ensure(ctx, ctx->ti_gcnt, sizeof(uint32_t) * (size_t)d));
+    SKM_TRY(ensure(ctx, ctx->ti_gptr, sizeof(int64_t) * ((size_t)d + 1)));
+    SKM_TRY(ensure(ctx, ctx->ti_hist, sizeof(uint32_t) * (size_t)k * TI_NB));
+    SKM_TRY(ensure(ctx, ctx->ti_mtab, (size_t)L * k * TI_NB));
+    SKM_TRY(ensure(ctx, ctx->ti_pbe, sizeof(uint32_t) * (size_t)L * d * TI_MB));
+    SKM_CUDA(cudaMemsetAsync(ctx->ti_hist.p, 0, sizeof(uint32_t) * (size_t)k * TI_NB, ctx->st));
+    SKM_CUDA(launch_ti_rows(P<float>(ctx->C32), ctx->ldc, d, k, P<uint32_t>(ctx->ti_G), P<uint32_t>(ctx->ti_gcnt),
+                            P<uint32_t>(ctx->ti_hist), ctx->st));
+    SKM_CUDA(launch_ti_scan(P<uint32_t>(ctx->ti_gcnt), d, P<int64_t>(ctx->ti_gptr), ctx->st));
+    TiThr thr{};
+    for (int l = 0; l < L; ++l) thr.v[l] = ctx->cfg.index_lambda[l] * ctx->cfg.index_lambda[l] * (1.0 - 1e-9);
+    SKM_CUDA(launch_ti_mtab(P<uint32_t>(ctx->ti_hist), nullptr, k, k, L, thr, P<uint8_t>(ctx->ti_mtab), ctx->st));
+    int64_t nz = 0;
+    SKM_CUDA(cudaMemcpyAsync(&nz, P<int64_t>(ctx->ti_gptr) + d, sizeof nz, cudaMemcpyDeviceToHost, ctx->st));
+    SKM_TRY(sync(ctx));
+    ctx->ti_nzC = nz > 0 ? nz : 1;
+    SKM_TRY(ensure(ctx, ctx->ti_P, sizeof(uint32_t) * (size_t)L * ctx->ti_nzC));
+    SKM_CUDA(launch_ti_fill(P<float>(ctx->C32), ctx->ldc, d, k, P<uint32_t>(ctx->ti_G), P<uint8_t>(ctx->ti_mtab), L,
+                            P<int64_t>(ctx->ti_gptr), ctx->ti_nzC, P<uint32_t>(ctx->ti_P), P<uint32_t>(ctx->ti_pbe),
+                            ctx->st));
+    ctx->stats.launches_total += 4;
+    ctx->ti_epoch = ctx->cent_epoch;
+    return SKM_OK;
+}
+
+// Query arguments over the resident index (lists and state filled in by the caller).
+TiQueryArgs ti_args(skm_ctx *ctx, const DevCsr &dc) {
+    TiQueryArgs q{};
+    q.row_ptr = dc.row_ptr;
+    q.col = dc.col;
+    q.val = dc.val;
+    q.C32 = P<float>(ctx->C32);
+    q.ldc = ctx->ldc;
+    q.k = ctx->cfg.k;
+    q.W = ti_words(ctx->cfg.k);
+    q.d = ctx->d;
+    q.G = P<uint32_t>(ctx->ti_G);
+    q.P = P<uint32_t>(ctx->ti_P);
+    q.nzC = ctx->ti_nzC;
+    q.gptr = P<int64_t>(ctx->ti_gptr);
+    q.pbe = P<uint32_t>(ctx->ti_pbe);
+    q.L = ctx->cfg.index_levels;
+    q.elt = ctx->cfg.precision == SKM_BF16 ? 2 : 4;
+    q.max_cands = ctx->cfg.index_max_cands;
+    for (int l = 0; l < q.L; ++l) q.lam[l] = ctx->cfg.index_lambda[l];
+    q.fixed_level = -1;
+    return q;
+}
+
 skm_status score_and_decide(skm_ctx *ctx, const DevCsr &dc, const int32_t *list, int32_t n_list,
                             bool pruned, int32_t n_moved, const int32_t *a_old, int32_t *a_new,
                             float *score_out) {
@@ -846,7 +906,7 @@ skm_status update_step(skm_ctx *ctx, const DevCsr &dc, const Postings &pg, const
         // clusters moved and the matrix is large (over 2 GB), the next step scores every
         // document in full instead
         const int64_t cm_bytes = (int64_t)ctx->d * n_moved * (ctx->cfg.precision == SKM_BF16 ? 2 : 4);
-        const bool build_cm = in_fit && ctx->cfg.prune == SKM_PRUNE_NCC &&
+        const bool build_cm = in_fit && ctx->cfg.prune != SKM_PRUNE_NONE &&
                               (n_moved <= k / 2 || cm_bytes <= (int64_t(2) << 30));
         u.C32 = P<float>(ctx->C32);
         u.C16 = ctx->cfg.precision == SKM_BF16 ? P<__nv_bfloat16>(ctx->C16) : nullptr;
@@ -899,15 +959,29 @@ void skm_config_default(skm_config *cfg, int32_t k) {
     cfg->rescore = 1;
     cfg->rescore_tau = 0.0;
     cfg->sparse_div = 0;
+    cfg->index_levels = 4;
+    cfg->index_lambda[0] = 0.1;
+    cfg->index_lambda[1] = 0.25;
+    cfg->index_lambda[2] = 0.4;
+    cfg->index_lambda[3] = 0.6;
+    cfg->index_min_changed = 100;
 }
 
 skm_status skm_create(const skm_config *cfg, skm_ctx **out) {
     if (!cfg || !out) return SKM_ERR_INVALID;
     *out = nullptr;
     if (cfg->k < 1 || cfg->max_iter < 1 || (cfg->precision != SKM_FP32 && cfg->precision != SKM_BF16) ||
-        (cfg->prune != SKM_PRUNE_NONE && cfg->prune != SKM_PRUNE_NCC) || !(cfg->rescore_tau >= 0.0) ||
-        (cfg->alloc == nullptr) != (cfg->free == nullptr) || cfg->sparse_div < 0)
+        (cfg->prune != SKM_PRUNE_NONE && cfg->prune != SKM_PRUNE_NCC && cfg->prune != SKM_PRUNE_NCC_INDEX) ||
+        cfg->index_max_cands < 0 ||
+        !(cfg->rescore_tau >= 0.0) || (cfg->alloc == nullptr) != (cfg->free == nullptr) || cfg->sparse_div < 0)
         return SKM_ERR_INVALID;
+    if (cfg->prune == SKM_PRUNE_NCC_INDEX) {
+        if (cfg->index_levels < 1 || cfg->index_levels > TI_MAXL) return SKM_ERR_INVALID;
+        for (int l = 0; l < cfg->index_levels; ++l)
+            if (!(cfg->index_lambda[l] > 0.0 && cfg->index_lambda[l] <= 1.0) ||
+                (l > 0 && !(cfg->index_lambda[l] > cfg->index_lambda[l - 1])))
+                return SKM_ERR_INVALID;
+    }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
         cudaGetLastError();
@@ -947,7 +1021,9 @@ skm_status skm_destroy(skm_ctx *ctx) {
                   &ctx->pos_in_m, &ctx->normsq, &ctx->inv_norm, &ctx->dot_fx, &ctx->newsq,
                   &ctx->rflag, &ctx->rtot, &ctx->rbase, &ctx->rptr_c, &ctx->rent_c, &ctx->rptr_m, &ctx->rent_m,
                   &ctx->colm, &ctx->skipped, &ctx->zflag, &ctx->zlist, &ctx->pp_dist, &ctx->pp_w, &ctx->pp_csum,
-                  &ctx->pp_drawn, &ctx->pp_seed, &ctx->pp_ids, &ctx->pp_u,
+                  &ctx->pp_drawn, &ctx->pp_seed, &ctx->pp_ids, &ctx->pp_u, &ctx->ti_G, &ctx->ti_gcnt,
+                  &ctx->ti_gptr, &ctx->ti_hist, &ctx->ti_mtab, &ctx->ti_P, &ctx->ti_pbe, &ctx->ti_stats,
+                  &ctx->ti_dump,
                   &ctx->normsq128, &ctx->sq128, &ctx->sq_store, &ctx->counters, &ctx->counters64, &ctx->scal,
                   &ctx->obj, &ctx->init_ids};
     for (Buf *b : all) release(ctx, *b);
@@ -1006,6 +1082,34 @@ skm_status skm_init_kmeanspp(skm_ctx *ctx, const skm_csr *docs, const double *un
     return sync(ctx);
 }
 
+skm_status skm_index_candidates(skm_ctx *ctx, const skm_csr *docs, int32_t level, uint32_t *bits) {
+    SKM_TRY(common_checks(ctx));
+    DeviceGuard g(ctx->cfg.device);
+    if (!bits) return fail(ctx, SKM_ERR_INVALID, "bits is NULL");
+    if (ctx->d == 0 || !ctx->C32.p) return fail(ctx, SKM_ERR_STATE, "no resident centroids");
+    if (ctx->cfg.k > TI_MAX_K) return fail(ctx, SKM_ERR_INVALID, "the threshold index serves k <= %d", TI_MAX_K);
+    if (ctx->cfg.index_levels < 1 || ctx->cfg.index_levels > TI_MAXL || level < 0 || level >= ctx->cfg.index_levels)
+        return fail(ctx, SKM_ERR_INVALID, "level %d outside [0, %d)", level, ctx->cfg.index_levels);
+    for (int l = 0; l < ctx->cfg.index_levels; ++l)
+        if (!(ctx->cfg.index_lambda[l] > 0.0 && ctx->cfg.index_lambda[l] <= 1.0))
+            return fail(ctx, SKM_ERR_INVALID, "index_lambda[%d] outside (0, 1]", l);
+    if (docs && docs->n_terms != ctx->d)
+        return fail(ctx, SKM_ERR_INVALID, "n_terms %d differs from the resident vocabulary %d", docs->n_terms, ctx->d);
+    DevCsr dc{};
+    SKM_TRY(stage_docs(ctx, docs, dc));
+    SKM_TRY(build_tindex(ctx));
+    const int32_t W = ti_words(ctx->cfg.k);
+    const size_t nb = sizeof(uint32_t) * (size_t)dc.n * W;
+    SKM_TRY(ensure(ctx, ctx->ti_dump, nb));
+    TiQueryArgs qa = ti_args(ctx, dc);
+    qa.n_list = dc.n;
+    qa.fixed_level = level;
+    qa.cand_out = P<uint32_t>(ctx->ti_dump);
+    SKM_CUDA(launch_ti_query(qa, ctx->st));
+    SKM_CUDA(cudaMemcpyAsync(bits, ctx->ti_dump.p, nb, cudaMemcpyDeviceToHost, ctx->st));
+    return sync(ctx);
+}
+
 skm_status skm_prepare_assign(skm_ctx *ctx) {
     if (!ctx) return SKM_ERR_INVALID;
     DeviceGuard g(ctx->cfg.device);
@@ -1044,6 +1148,7 @@ skm_status skm_fit(skm_ctx *ctx, const skm_csr *docs, const int32_t *init_doc_id
     ctx->ev_score.clear();
     ctx->ev_decide.clear();
     ctx->ev_update.clear();
+    ctx->ev_query.clear();
     ctx->ev_next = 0;
     DevCsr dc{};
     SKM_TRY(stage_docs(ctx, docs, dc));
@@ -1069,7 +1174,12 @@ skm_status skm_fit(skm_ctx *ctx, const skm_csr *docs, const int32_t *init_doc_id
     SKM_CUDA(launch_order_by_length(dc.row_ptr, N, P<int32_t>(ctx->order_hist), P<int32_t>(ctx->order), ctx->st));
     ctx->stats.launches_total += 3;
 
-    const bool prune = ctx->cfg.prune == SKM_PRUNE_NCC;
+    const bool prune = ctx->cfg.prune != SKM_PRUNE_NONE;
+    const bool use_index = ctx->cfg.prune == SKM_PRUNE_NCC_INDEX && k <= TI_MAX_K;
+    if (use_index) {
+        SKM_TRY(ensure(ctx, ctx->ti_stats, 4 * sizeof(unsigned long long)));
+        SKM_CUDA(cudaMemsetAsync(ctx->ti_stats.p, 0, 4 * sizeof(unsigned long long), ctx->st));
+    }
     int32_t n_moved_prev = k;
     int32_t it = 0;
     int cur = 0;
@@ -1081,8 +1191,40 @@ skm_status skm_fit(skm_ctx *ctx, const skm_csr *docs, const int32_t *init_doc_id
         SKM_TRY(reset_counters(ctx));
         int32_t n_pruned = 0, n_full = (int32_t)N;
         const int32_t *full_list = P<int32_t>(ctx->order);
-        // the pruned pass needs the compacted matrix of the last update's moved list
-        if (prune && !first && ctx->cm_valid) {
+        // Sec. 3.2: the threshold index decides the documents whose baseline reaches a
+        // threshold when enough centroids changed (Sec. 4.3); the rest go to the dense passes
+        const bool index_step = use_index && !first &&
+                                (ctx->cfg.index_min_changed < 0 || n_moved_prev > ctx->cfg.index_min_changed);
+        if (index_step) {
+            SKM_TRY(build_tindex(ctx));
+            SKM_CUDA(cudaMemcpyAsync(a_new, a_old, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, ctx->st));
+            TiQueryArgs qa = ti_args(ctx, dc);
+            qa.n_list = N;
+            qa.list = P<int32_t>(ctx->order);
+            qa.a_old = a_old;
+            qa.changed = P<uint8_t>(ctx->changed);
+            qa.ncc = 1;
+            qa.prune_fallback = ctx->cm_valid ? 1 : 0;
+            qa.a_new = a_new;
+            qa.s_state = P<float>(ctx->s_state);
+            qa.r_state = P<float>(ctx->r_state);
+            qa.clean = P<uint8_t>(ctx->clean);
+            qa.counters = P<int32_t>(ctx->counters);
+            qa.counters64 = P<unsigned long long>(ctx->counters64);
+            qa.pruned_list = P<int32_t>(ctx->list_a);
+            qa.full_list = P<int32_t>(ctx->list_b);
+            qa.stats = P<unsigned long long>(ctx->ti_stats);
+            {
+                Timed tm(ctx, ctx->ev_query);
+                SKM_CUDA(launch_ti_query(qa, ctx->st));
+            }
+            ctx->stats.launches_total++;
+            SKM_TRY(read_counters(ctx));
+            n_pruned = ctx->h_counters[CNT_PRUNED];
+            n_full = ctx->h_counters[CNT_FULL];
+            full_list = P<int32_t>(ctx->list_b);
+        } else if (prune && !first && ctx->cm_valid) {
+            // the pruned pass needs the compacted matrix of the last update's moved list
             PartitionArgs pa{};
             pa.n_docs = N;
             pa.order = P<int32_t>(ctx->order);
@@ -1103,7 +1245,7 @@ skm_status skm_fit(skm_ctx *ctx, const skm_csr *docs, const int32_t *init_doc_id
             full_list = P<int32_t>(ctx->list_b);
         }
         // pruned documents keep a_old unless the decision moves them; copy it first
-        if (n_pruned > 0) SKM_CUDA(cudaMemcpyAsync(a_new, a_old, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, ctx->st));
+        if (n_pruned > 0 && !index_step) SKM_CUDA(cudaMemcpyAsync(a_new, a_old, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, ctx->st));
         SKM_TRY(score_and_decide(ctx, dc, full_list, n_full, false, k, a_old, a_new, nullptr));
         SKM_TRY(score_and_decide(ctx, dc, P<int32_t>(ctx->list_a), n_pruned, true, n_moved_prev, a_old, a_new, nullptr));
         ctx->stats.docs_full += n_full;
@@ -1112,7 +1254,7 @@ skm_status skm_fit(skm_ctx *ctx, const skm_csr *docs, const int32_t *init_doc_id
         ctx->stats.sims += (int64_t)n_full * k + (int64_t)n_pruned * n_moved_prev;
         SKM_TRY(read_counters(ctx));
         const int64_t nnz_pruned = n_pruned > 0 ? (int64_t)ctx->h_counters64[C64_NNZ_PRUNED] : 0;
-        const int64_t nnz_full = dc.nnz - nnz_pruned;
+        const int64_t nnz_full = index_step ? (int64_t)ctx->h_counters64[C64_NNZ_FULL] : dc.nnz - nnz_pruned;
         const int32_t n_refull = ctx->h_counters[CNT_REFULL];
         const int64_t nnz_refull = n_refull > 0 ? (int64_t)ctx->h_counters64[C64_NNZ_REFULL] : 0;
         if (n_refull > 0) {
@@ -1125,8 +1267,9 @@ skm_status skm_fit(skm_ctx *ctx, const skm_csr *docs, const int32_t *init_doc_id
         // needed centroid element once (rows of present terms x scored columns)
         const int64_t elt = ctx->cfg.precision == SKM_BF16 ? 2 : 4;
         ctx->stats.fmas += nnz_full * k + nnz_pruned * n_moved_prev + nnz_refull * k;
-        const int32_t cols_needed = (n_full > 0 || n_refull > 0) ? k : n_moved_prev;
-        ctx->stats.bytes += 8 * (dc.nnz + nnz_refull) + 20 * (N + n_refull) + pg.d_eff * cols_needed * elt;
+        const int32_t cols_needed = (n_full > 0 || n_refull > 0) ? k : (n_pruned > 0 ? n_moved_prev : 0);
+        ctx->stats.bytes += 8 * (nnz_full + nnz_pruned + nnz_refull) + 20 * ((int64_t)n_full + n_pruned + n_refull) +
+                            pg.d_eff * cols_needed * elt;
         SKM_TRY(rescore_queues(ctx, dc, a_new, nullptr));
         bool converged = false;
         SKM_TRY(update_step(ctx, dc, pg, a_new, a_old, N, first, true, &converged, t - 1, true));
@@ -1148,6 +1291,16 @@ skm_status skm_fit(skm_ctx *ctx, const skm_csr *docs, const int32_t *init_doc_id
     SKM_TRY(sync(ctx));
     collect_times(ctx);
     ctx->stats.iters = it;
+    if (use_index) {
+        unsigned long long h[4];
+        SKM_CUDA(cudaMemcpyAsync(h, ctx->ti_stats.p, sizeof h, cudaMemcpyDeviceToHost, ctx->st));
+        SKM_TRY(sync(ctx));
+        ctx->stats.index_docs = (int64_t)h[0];
+        ctx->stats.index_sims = (int64_t)h[1];
+        ctx->stats.index_entries = (int64_t)h[2];
+        ctx->stats.index_products = (int64_t)h[3];
+        ctx->stats.sims += (int64_t)h[1];
+    }
     {
         int64_t sk = 0;
         SKM_TRY(read_skipped(ctx, &sk));

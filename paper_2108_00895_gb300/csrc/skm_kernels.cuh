@@ -19,7 +19,7 @@ enum {
     CNT_N = 9
 };
 // 64-bit device counters (nonzeros of listed documents, for the work counts).
-enum { C64_NNZ_PRUNED = 0, C64_NNZ_REFULL = 1, C64_N = 2 };
+enum { C64_NNZ_PRUNED = 0, C64_NNZ_REFULL = 1, C64_NNZ_FULL = 2, C64_N = 3 };
 
 struct DecideArgs {
     int32_t n_list;
@@ -185,6 +185,71 @@ cudaError_t launch_finish(const int32_t *pos_in_m, const int32_t *sizes, int32_t
                           const unsigned long long *dot_fx, double inv_dot_scale, const double *normsq,
                           const double *newsq, double *norm_store, double *sq_store, double *obj_out,
                           double *shift_out, cudaStream_t st);
+// ---------------------------------------------------------------- threshold index (tindex.cu)
+// Sec. 3.2 on the GPU: bitmap G, per-centroid value bins, minimum-overlap bounds and the
+// term-major lists P_lambda; see tindex.cu for the layout and the bound.
+constexpr int TI_NB = 512;     // value bins per centroid
+constexpr int TI_MAXL = 4;     // thresholds (lambda levels)
+constexpr int TI_MB = 8;       // m buckets of each term's list
+constexpr int TI_PLANES = 8;   // bits of the overlap counts and of the stored m bounds
+constexpr int32_t TI_MAX_K = 16384;
+__host__ __device__ constexpr int32_t ti_words(int32_t k) { return (k + 31) / 32; }
+
+struct TiThr {
+    double v[TI_MAXL];   // lambda_l^2 (1 - 1e-9)
+};
+
+struct TiQueryArgs {
+    int64_t n_list;
+    const int32_t *list;        // nullable: identity
+    const int64_t *row_ptr;
+    const int32_t *col;
+    const float *val;
+    const float *C32;
+    int64_t ldc;
+    int32_t k;
+    int32_t W;                  // ti_words(k)
+    int32_t d;
+    const uint32_t *G;          // [d][W]
+    const uint32_t *P;          // [L][nzC]
+    int64_t nzC;
+    const int64_t *gptr;        // [d + 1] row offsets of G's nonzeros
+    const uint32_t *pbe;        // [L][d][TI_MB] bucket ends of each term's list
+    int L;
+    int elt;                    // bytes per entry of the dense scored copy (2 BF16, 4 FP32)
+    int max_cands;              // > 0: candidate cap (at most 512); 0: min(512, k elt / 32)
+    double lam[TI_MAXL];        // ascending
+    int fixed_level;            // >= 0: candidate dump at this level (no baseline, no scoring)
+    uint32_t *cand_out;         // candidate dump: [document][W] bits
+    const int32_t *a_old;
+    const uint8_t *changed;     // per centroid: moved in the last update
+    int ncc;                    // 1: combine with Sec. 3.1
+    int prune_fallback;         // 1: unindexed documents may go to the pruned list
+    int32_t *a_new;
+    float *s_state;
+    float *r_state;
+    uint8_t *clean;
+    float *score_out;           // nullable
+    int32_t *counters;
+    unsigned long long *counters64;
+    int32_t *pruned_list;
+    int32_t *full_list;
+    unsigned long long *stats;  // nullable: [documents, similarities, P entries walked, products]
+};
+
+// G, row counts and bin counts of every centroid (hist zeroed by the caller).
+cudaError_t launch_ti_rows(const float *C, int64_t ldc, int32_t d, int32_t k, uint32_t *G, uint32_t *gcnt,
+                           uint32_t *hist, cudaStream_t st);
+// out[0..n] = exclusive prefix sums of in[0..n), out[n] = total.
+cudaError_t launch_ti_scan(const uint32_t *in, int64_t n, int64_t *out, cudaStream_t st);
+// m bounds of the listed centroids (list NULL: centroids 0..n-1).
+cudaError_t launch_ti_mtab(const uint32_t *hist, const int32_t *list, int32_t n, int32_t k, int L, const TiThr &thr,
+                           uint8_t *mtab, cudaStream_t st);
+cudaError_t launch_ti_fill(const float *C, int64_t ldc, int32_t d, int32_t k, const uint32_t *G, const uint8_t *mtab,
+                           int L, const int64_t *gptr, int64_t nzC, uint32_t *P, uint32_t *pbe, cudaStream_t st);
+size_t ti_query_smem(int32_t k);
+cudaError_t launch_ti_query(const TiQueryArgs &a, cudaStream_t st);
+
 // Squared norms of the stored FP32 columns.
 cudaError_t launch_col_sq(const float *C32, int64_t ldc, int32_t d, int32_t k, double *out,
                           cudaStream_t st);

@@ -1,0 +1,593 @@
+// Threshold index of Sec. 3.2 (the dot product indexing structure) on the GPU.
+//
+// Lemma 3.1: if x . c >= lambda ||x|| then the squares of c over the nonzero terms of x sum
+// to at least lambda^2. Sec. 3.2 turns this into a candidate filter: with the entries of a
+// centroid sorted by decreasing value, an entry at rank p can only start an overlap that
+// reaches lambda if the document shares at least m_p terms with the centroid, m_p being the
+// number of entries from p on whose squares first reach lambda^2 (no entry of higher rank
+// needs to be counted: it would have started the overlap itself). The index P_lambda maps a
+// term to the (centroid, m) pairs of its entries; the general index G maps it to the
+// centroids with a nonzero there, giving the overlap counts of a query.
+//
+// GPU form:
+//   G        a term-major bitmap, word w of row t holds the nonzero flags of centroids
+//            32w .. 32w + 31; a document's overlap counts are bit-sliced 8-bit counters
+//            over the words of its terms' rows (k / 8 bytes read per term), saturating at
+//            255 for documents with more nonzeros.
+//   m bound  instead of sorting each centroid, its entries are counted in 512 bins of |value|
+//            (16 per octave: the float bits >> 19). For an entry in bin b, the entries from
+//            its rank on are bounded above by the bins' upper edges: the entry's own bin
+//            counted whole, then the lower bins. The smallest count whose bounded squares
+//            reach lambda^2 is a lower bound of m_p, so the candidates are a superset of the
+//            paper's; an entry whose bounded tail cannot reach lambda^2 is left out of
+//            P_lambda, as the paper leaves out the entries after it stops. m is stored
+//            clamped to 255 (8 bits), which again only adds candidates.
+//   P_lambda term-major lists of (centroid << 8 | m), one set of lists per lambda, each term's
+//            list at the offset of its row in G's nonzero count (capacity |G_t| per level),
+//            ordered by m in 8 buckets of doubling width, so that a document walks only the
+//            entries whose m its number of terms can reach.
+//   query    one warp per document: the baseline x . c_{a_old} (FP64), the largest lambda
+//            below it (scaled by ||x||), the overlap counts, the walk of P_lambda over the
+//            document's terms, and FP64 scores of the candidates over the terms where G says
+//            the centroid is nonzero, in CSR order with one fused multiply-add per term
+//            (skipped terms contribute exact zeros, so the sum equals the full CSR-order
+//            sum). Combined with Sec. 3.1: a document whose cluster did not change keeps only
+//            candidates that changed.
+//   Documents without a threshold below their baseline are appended to the lists of the
+//   dense passes, classified as the Sec. 3.1 partition does.
+#include <cmath>
+
+#include "skm_kernels.cuh"
+
+namespace skm {
+
+constexpr int TI_WARPS = 8;
+constexpr uint32_t TI_KEY0 = 1536;   // float bits >> 19 of 2^-31, the lowest bin's lower edge
+
+constexpr int TI_STAGE = 64;   // most nonzeros of a document the query serves
+constexpr int TI_CAND = 512;   // most candidates it scores
+
+// Shared-memory words of one query warp (layout in ti_warp_smem), a multiple of 4 words.
+__host__ __device__ constexpr int64_t ti_warp_words(int32_t W) {
+    return ((int64_t)7 * TI_STAGE + 4 + TI_CAND + (int64_t)(TI_PLANES + 1) * W + 3) & ~int64_t(3);
+}
+
+// m bucket: 0 for m = 1, b for m in (2^(b-1), 2^b], TI_MB - 1 for m > 2^(TI_MB - 2).
+__host__ __device__ __forceinline__ int ti_mbucket(uint32_t m) {
+    int b = 0;
+    while (b < TI_MB - 1 && (1u << b) < m) ++b;
+    return b;
+}
+
+__device__ __forceinline__ int ti_bin(float v) {
+    const int key = (int)(__float_as_uint(fabsf(v)) >> 19) - (int)TI_KEY0;
+    return key < 0 ? 0 : (key > TI_NB - 1 ? TI_NB - 1 : key);
+}
+
+// Upper edge of bin b (every |value| in the bin is below it); the top bin is open.
+__device__ __forceinline__ double ti_hi(int b) {
+    return b >= TI_NB - 1 ? INFINITY : (double)__uint_as_float((uint32_t)(b + TI_KEY0 + 1) << 19);
+}
+
+// ------------------------------------------------------------------------------------
+// Build pass 1: one warp per row t (grid-stride). Bitmap words, the row's nonzero count,
+// and one count per nonzero in its centroid's bin (integer atomics: order-independent).
+// ------------------------------------------------------------------------------------
+__global__ void k_ti_rows(const float *C, int64_t ldc, int32_t d, int32_t k, int32_t W, uint32_t *G,
+                          uint32_t *gcnt, uint32_t *hist) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    constexpr int U = 4;
+    for (int64_t t = warp; t < d; t += nwarps) {
+        const float *row = C + t * ldc;
+        uint32_t tot = 0;
+        for (int w0 = 0; w0 < W; w0 += U) {
+            float v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int j = (w0 + u) * 32 + lane;
+                v[u] = (w0 + u < W && j < k) ? __ldg(row + j) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (w0 + u >= W) break;
+                const unsigned nz = __ballot_sync(FULL, v[u] != 0.f);
+                if (lane == 0) G[t * W + w0 + u] = nz;
+                tot += __popc(nz);
+                if (v[u] != 0.f) atomicAdd(hist + (size_t)((w0 + u) * 32 + lane) * TI_NB + ti_bin(v[u]), 1u);
+            }
+        }
+        if (lane == 0) gcnt[t] = tot;
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Exclusive prefix sums of n uint32 counts into int64 offsets (out[n] = total): one block,
+// tiles of 1024 x 4 elements in order (deterministic).
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_ti_scan(const uint32_t *in, int64_t n, int64_t *out) {
+    __shared__ int64_t part[1024];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t b0 = 0; b0 < n; b0 += 4096) {
+        const int64_t i0 = b0 + (int64_t)threadIdx.x * 4;
+        int64_t v[4], s = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            v[q] = i0 + q < n ? (int64_t)in[i0 + q] : 0;
+            s += v[q];
+        }
+        part[threadIdx.x] = s;
+        __syncthreads();
+        for (int off = 1; off < 1024; off <<= 1) {
+            const int64_t o = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0;
+            __syncthreads();
+            part[threadIdx.x] += o;
+            __syncthreads();
+        }
+        int64_t run = carry + part[threadIdx.x] - s;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (i0 + q < n) out[i0 + q] = run;
+            run += v[q];
+        }
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += part[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[n] = carry;
+}
+
+// ------------------------------------------------------------------------------------
+// Build pass 2: one block per listed centroid, one thread per bin. With S(b) and N(b) the
+// inclusive sums over bins <= b of count x upper edge^2 and of count, an entry in bin b
+// reaches thr from the top of its bin through bins b .. e: e is the largest bin with
+// S(b) - S(e - 1) >= thr, and the bound is N(b) - N(e) whole entries of bins above e plus
+// ceil((thr - (S(b) - S(e))) / edge_e^2) entries of bin e. S(b) < thr: not in P.
+// thr = lambda^2 (1 - 1e-9): the rounding of the double sums cannot raise a bound.
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(TI_NB) k_ti_mtab(const uint32_t *hist, const int32_t *list, int32_t k, int L,
+                                                   TiThr thr, uint8_t *mtab) {
+    __shared__ double S[TI_NB];
+    __shared__ uint32_t N[TI_NB];
+    const int j = list ? list[blockIdx.x] : (int)blockIdx.x;
+    const int b = threadIdx.x;
+    const uint32_t c = hist[(size_t)j * TI_NB + b];
+    const double h = ti_hi(b);
+    const double h2 = h * h;
+    S[b] = c ? (double)c * h2 : 0.0;
+    N[b] = c;
+    __syncthreads();
+    for (int off = 1; off < TI_NB; off <<= 1) {
+        const double so = b >= off ? S[b - off] : 0.0;
+        const uint32_t no = b >= off ? N[b - off] : 0u;
+        __syncthreads();
+        S[b] += so;
+        N[b] += no;
+        __syncthreads();
+    }
+    for (int l = 0; l < L; ++l) {
+        uint32_t m = 0;
+        if (c && b == TI_NB - 1) {
+            m = 1;   // open bin: no bound on the value
+        } else if (c && S[b] >= thr.v[l]) {
+            const double base = S[b] - thr.v[l];
+            // e = first index in [0, b) with S[e] > base (b if none)
+            int lo = 0, hi = b;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (S[mid] > base) hi = mid;
+                else lo = mid + 1;
+            }
+            const int e = lo;
+            const double rem = thr.v[l] - (S[b] - S[e]);
+            const double he = ti_hi(e);
+            double need = ceil(rem / (he * he));
+            if (!(need >= 0.0)) need = 0.0;
+            const double q = (double)(N[b] - N[e]) + need;
+            m = q < 1.0 ? 1u : (q > 255.0 ? 255u : (uint32_t)q);
+        }
+        mtab[((size_t)l * k + j) * TI_NB + b] = (uint8_t)m;
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Build pass 3: one warp per row t, one level at a time. Reads only the nonzeros (the
+// bitmap says where), counts the level's entries per m bucket (bucket b holds m in
+// (2^(b-1), 2^b], the last one m > 64), then writes (j << 8 | m) bucket by bucket, in
+// centroid order within a bucket; pbe[(l d + t) TI_MB + b] = end of bucket b in the row's
+// list. A document of n nonzeros has counts <= n, so it walks only the buckets up to n's.
+// ------------------------------------------------------------------------------------
+__global__ void k_ti_fill(const float *C, int64_t ldc, int32_t d, int32_t k, int32_t W, const uint32_t *G,
+                          const uint8_t *mtab, int L, const int64_t *gptr, int64_t nzC, uint32_t *P,
+                          uint32_t *pbe) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const unsigned below = (1u << lane) - 1u;
+    for (int64_t t = warp; t < d; t += nwarps) {
+        const float *row = C + t * ldc;
+        const int64_t base = gptr[t];
+        for (int l = 0; l < L; ++l) {
+            const uint8_t *ml = mtab + (size_t)l * k * TI_NB;
+            uint32_t cnt[TI_MB];
+#pragma unroll
+            for (int b = 0; b < TI_MB; ++b) cnt[b] = 0u;
+            for (int w = 0; w < W; ++w) {
+                const uint32_t g = __ldg(G + t * W + w);
+                if (g == 0u) continue;
+                const int j = w * 32 + lane;
+                const bool nz = (g >> lane) & 1u;
+                const uint32_t m = nz ? (uint32_t)__ldg(ml + (size_t)j * TI_NB + ti_bin(__ldg(row + j))) : 0u;
+                const int bid = m ? ti_mbucket(m) : -1;
+#pragma unroll
+                for (int b = 0; b < TI_MB; ++b) cnt[b] += __popc(__ballot_sync(FULL, bid == b));
+            }
+            uint32_t at[TI_MB];
+            uint32_t run = 0u;
+#pragma unroll
+            for (int b = 0; b < TI_MB; ++b) {
+                at[b] = run;
+                run += cnt[b];
+                if (lane == b) pbe[((int64_t)l * d + t) * TI_MB + b] = run;
+            }
+            uint32_t *Pl = P + (int64_t)l * nzC + base;
+            for (int w = 0; w < W; ++w) {
+                const uint32_t g = __ldg(G + t * W + w);
+                if (g == 0u) continue;
+                const int j = w * 32 + lane;
+                const bool nz = (g >> lane) & 1u;
+                const uint32_t m = nz ? (uint32_t)__ldg(ml + (size_t)j * TI_NB + ti_bin(__ldg(row + j))) : 0u;
+                const int bid = m ? ti_mbucket(m) : -1;
+#pragma unroll
+                for (int b = 0; b < TI_MB; ++b) {
+                    const unsigned bal = __ballot_sync(FULL, bid == b);
+                    if (bid == b) Pl[at[b] + __popc(bal & below)] = ((uint32_t)j << 8) | m;
+                    at[b] += __popc(bal);
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Query: one warp per listed document (grid-stride). A document of at most TI_STAGE
+// nonzeros is staged in shared memory, and every phase issues its loads in independent
+// batches (the baseline's entries, the bitmap words of 8 terms at a time, 4 list entries
+// at a time, a candidate's entries for 8 terms at a time), so that a warp waits for a
+// few memory round trips per document rather than one per term.
+// Shared memory per warp (32-bit words): the staged terms, values and baseline entries,
+// the list offsets (64-bit), lengths and prefix sums; the 8 count planes of each bitmap
+// word (word w's at [8w, 8w + 8), read as two 16-byte vectors), the candidate bits and
+// the candidate list; rounded up to 16 bytes.
+// A document goes to the dense passes when no threshold is below its baseline, when it
+// has more than TI_STAGE nonzeros, or when its candidates would cost more to score one
+// by one (a 32-byte sector per product) than a dense pass over all k (elt bytes per
+// product): more than min(TI_CAND, k elt / 32) candidates (or the configured cap).
+// ------------------------------------------------------------------------------------
+struct TiWarpSmem {
+    int32_t *t;
+    float *x;
+    float *cb0;     // baseline entries c_{a_old}
+    int64_t *off;
+    uint32_t *len;
+    uint32_t *pre;  // [TI_STAGE + 1]
+    uint32_t *pl;   // [8 W]
+    uint32_t *cb;   // [W]
+    int32_t *cl;    // [TI_CAND]
+};
+
+__device__ __forceinline__ TiWarpSmem ti_warp_smem(uint32_t *base, int W) {
+    TiWarpSmem s;
+    uint32_t *q = base;
+    s.off = reinterpret_cast<int64_t *>(q);
+    q += 2 * TI_STAGE;
+    s.t = reinterpret_cast<int32_t *>(q);
+    q += TI_STAGE;
+    s.x = reinterpret_cast<float *>(q);
+    q += TI_STAGE;
+    s.cb0 = reinterpret_cast<float *>(q);
+    q += TI_STAGE;
+    s.len = q;
+    q += TI_STAGE;
+    s.pre = q;
+    q += TI_STAGE + 4;
+    s.cl = reinterpret_cast<int32_t *>(q);
+    q += TI_CAND;
+    s.pl = q;
+    q += TI_PLANES * W;
+    s.cb = q;
+    return s;
+}
+
+__device__ __forceinline__ void ti_fallback(const TiQueryArgs &a, int32_t i, int32_t a0, int64_t nnz) {
+    const bool pr = a.prune_fallback && a.clean[i] && !a.changed[a0];
+    if (pr) {
+        a.pruned_list[atomicAdd(&a.counters[CNT_PRUNED], 1)] = i;
+        atomicAdd(a.counters64 + C64_NNZ_PRUNED, (unsigned long long)nnz);
+    } else {
+        a.full_list[atomicAdd(&a.counters[CNT_FULL], 1)] = i;
+        atomicAdd(a.counters64 + C64_NNZ_FULL, (unsigned long long)nnz);
+    }
+}
+
+__global__ void __launch_bounds__(TI_WARPS * 32) k_ti_query(TiQueryArgs a) {
+    extern __shared__ __align__(16) uint32_t ti_sm[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int W = a.W;
+    const TiWarpSmem sm = ti_warp_smem(ti_sm + (size_t)wib * ti_warp_words(W), W);
+    __shared__ int ncand[TI_WARPS];
+    unsigned long long n_docs = 0, n_sims = 0, n_walk = 0, n_prod = 0;
+    const int64_t nw = (int64_t)gridDim.x * TI_WARPS;
+    const int cand_cap = a.max_cands > 0 ? min(TI_CAND, a.max_cands) : min(TI_CAND, (int)((int64_t)a.k * a.elt / 32));
+    for (int64_t pos = (int64_t)blockIdx.x * TI_WARPS + wib; pos < a.n_list; pos += nw) {
+        const int32_t i = a.list ? a.list[pos] : (int32_t)pos;
+        const int64_t beg = a.row_ptr[i];
+        const int nnz64 = (int)min(a.row_ptr[i + 1] - beg, (int64_t)TI_STAGE + 1);
+        const int32_t a0 = a.a_old ? a.a_old[i] : -1;
+        if (nnz64 > TI_STAGE) {
+            if (a.cand_out) {   // candidate dump: long documents are not indexed
+                for (int w = lane; w < W; w += 32) a.cand_out[(int64_t)i * W + w] = 0xffffffffu;
+            } else if (lane == 0) {
+                ti_fallback(a, i, a0, a.row_ptr[i + 1] - beg);
+            }
+            __syncwarp();
+            continue;
+        }
+        const int nnz = nnz64;
+        // stage the document (and the baseline's centroid entries)
+        for (int p = lane; p < nnz; p += 32) {
+            const int32_t t = __ldg(a.col + beg + p);
+            sm.t[p] = t;
+            sm.x[p] = __ldg(a.val + beg + p);
+            if (a0 >= 0) sm.cb0[p] = __ldg(a.C32 + (int64_t)t * a.ldc + a0);
+        }
+        if (lane == 0) ncand[wib] = 0;
+        __syncwarp();
+        int lev = a.fixed_level;
+        double sb = -INFINITY;
+        if (lev < 0) {
+            double s = 0.0, ss = 0.0;
+            if (lane == 0)
+                for (int p = 0; p < nnz; ++p) {
+                    const double x = (double)sm.x[p];
+                    s = fma(x, (double)sm.cb0[p], s);
+                    ss = fma(x, x, ss);
+                }
+            sb = __shfl_sync(FULL, s, 0);
+            const double xn = sqrt(__shfl_sync(FULL, ss, 0));
+            for (int l = a.L - 1; l >= 0; --l)
+                if (a.lam[l] * xn * (1.0 + 1e-9) <= sb) {
+                    lev = l;
+                    break;
+                }
+            if (lev < 0) {
+                if (lane == 0) ti_fallback(a, i, a0, nnz);
+                __syncwarp();
+                continue;
+            }
+        }
+        // list offsets and lengths of the document's terms at this level
+        // entries with m > nnz cannot pass (counts are at most nnz): walk the buckets up to nnz's
+        const uint32_t *pbe = a.pbe + (int64_t)lev * a.d * TI_MB + ti_mbucket((uint32_t)nnz);
+        for (int p = lane; p < nnz; p += 32) {
+            const int32_t t = sm.t[p];
+            sm.off[p] = __ldg(a.gptr + t);
+            sm.len[p] = __ldg(pbe + (int64_t)t * TI_MB);
+        }
+        // overlap counts: bit-sliced 8-bit counters (ripple-carry adds; nnz <= 64 < 256),
+        // lane-owned words, bitmap words of 8 terms loaded at a time
+        for (int w = lane; w < W; w += 32) {
+            uint32_t c[TI_PLANES];
+#pragma unroll
+            for (int q = 0; q < TI_PLANES; ++q) c[q] = 0u;
+            for (int p0 = 0; p0 < nnz; p0 += 8) {
+                uint32_t g[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    g[u] = p0 + u < nnz ? __ldg(a.G + (int64_t)sm.t[p0 + u] * W + w) : 0u;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    uint32_t cy = g[u];
+#pragma unroll
+                    for (int q = 0; q < TI_PLANES; ++q) {
+                        const uint32_t nq = c[q] ^ cy;
+                        cy &= c[q];
+                        c[q] = nq;
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < TI_PLANES; ++q) sm.pl[TI_PLANES * w + q] = c[q];
+            sm.cb[w] = 0u;
+        }
+        __syncwarp();
+        if (lane == 0) {
+            uint32_t run = 0;
+            for (int p = 0; p < nnz; ++p) {
+                sm.pre[p] = run;
+                run += sm.len[p];
+            }
+            sm.pre[nnz] = run;
+        }
+        __syncwarp();
+        // walk P_lambda over the document's terms as one flat list of entries
+        const uint32_t E = sm.pre[nnz];
+        n_walk += (lane == 0) ? E : 0u;
+        const uint32_t *Pl = a.P + (int64_t)lev * a.nzC;
+        const bool nccf = a.ncc && a0 >= 0 && !a.changed[a0];
+        int pc = 0;   // this lane's term: the last p with pre[p] <= q (q only grows)
+        for (uint32_t q0 = lane; q0 < E; q0 += 32 * 4) {
+            uint32_t pe[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t q = q0 + 32u * u;
+                pe[u] = 0u;
+                if (q < E) {
+                    while (pc + 1 < nnz && sm.pre[pc + 1] <= q) ++pc;
+                    pe[u] = __ldg(Pl + sm.off[pc] + (q - sm.pre[pc]));
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (q0 + 32u * u >= E) break;
+                const int j = (int)(pe[u] >> 8);
+                const uint32_t m = pe[u] & 255u;
+                const int w = j >> 5, b = j & 31;
+                const uint4 lo4 = *reinterpret_cast<const uint4 *>(sm.pl + TI_PLANES * w);
+                const uint4 hi4 = *reinterpret_cast<const uint4 *>(sm.pl + TI_PLANES * w + 4);
+                const uint32_t c = ((lo4.x >> b) & 1u) | (((lo4.y >> b) & 1u) << 1) | (((lo4.z >> b) & 1u) << 2) |
+                                   (((lo4.w >> b) & 1u) << 3) | (((hi4.x >> b) & 1u) << 4) |
+                                   (((hi4.y >> b) & 1u) << 5) | (((hi4.z >> b) & 1u) << 6) |
+                                   (((hi4.w >> b) & 1u) << 7);
+                if (c >= m && j != a0 && (!nccf || a.changed[j])) atomicOr(sm.cb + w, 1u << b);
+            }
+        }
+        __syncwarp();
+        if (a.cand_out) {
+            for (int w = lane; w < W; w += 32) a.cand_out[(int64_t)i * W + w] = sm.cb[w];
+            __syncwarp();
+            continue;
+        }
+        // candidate list (its order does not matter: the argmax below is order-free)
+        for (int w = lane; w < W; w += 32) {
+            uint32_t bits = sm.cb[w];
+            if (!bits) continue;
+            int at = atomicAdd(&ncand[wib], __popc(bits));
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1u;
+                if (at < TI_CAND) sm.cl[at] = w * 32 + b;
+                ++at;
+            }
+        }
+        __syncwarp();
+        const int nc = ncand[wib];
+        if (nc > cand_cap) {
+            if (lane == 0) ti_fallback(a, i, a0, nnz);
+            __syncwarp();
+            continue;
+        }
+        // FP64 scores of the candidates: one fused multiply-add per term in CSR order
+        // (entries that are zero add exactly nothing); lanes own candidates
+        double best = -INFINITY;
+        int bj = INT32_MAX;
+        if (lane == 0) {
+            best = sb;
+            bj = a0;
+        }
+        for (int c = lane; c < nc; c += 32) {
+            const int j = sm.cl[c];
+            double acc = 0.0;
+            for (int p0 = 0; p0 < nnz; p0 += 8) {
+                float v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    v[u] = p0 + u < nnz ? __ldg(a.C32 + (int64_t)sm.t[p0 + u] * a.ldc + j) : 0.f;
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (p0 + u < nnz) acc = fma((double)sm.x[p0 + u], (double)v[u], acc);
+            }
+            n_prod += (unsigned long long)nnz;
+            ++n_sims;
+            if (better64(acc, j, best, bj)) {
+                best = acc;
+                bj = j;
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const double os = __shfl_xor_sync(FULL, best, off);
+            const int oj = __shfl_xor_sync(FULL, bj, off);
+            if (better64(os, oj, best, bj)) {
+                best = os;
+                bj = oj;
+            }
+        }
+        if (lane == 0) {
+            a.a_new[i] = bj;
+            a.s_state[i] = (float)best;
+            a.r_state[i] = 0.f;
+            a.clean[i] = 0;   // the dense passes' stored bounds do not describe this decision
+            if (a.score_out) a.score_out[i] = (float)best;
+            ++n_docs;
+            ++n_sims;   // the baseline
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        n_docs += __shfl_xor_sync(FULL, n_docs, off);
+        n_sims += __shfl_xor_sync(FULL, n_sims, off);
+        n_walk += __shfl_xor_sync(FULL, n_walk, off);
+        n_prod += __shfl_xor_sync(FULL, n_prod, off);
+    }
+    if (lane == 0 && a.stats) {
+        if (n_docs) atomicAdd(a.stats + 0, n_docs);
+        if (n_sims) atomicAdd(a.stats + 1, n_sims);
+        if (n_walk) atomicAdd(a.stats + 2, n_walk);
+        if (n_prod) atomicAdd(a.stats + 3, n_prod);
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Launchers
+// ------------------------------------------------------------------------------------
+static unsigned row_blocks(int64_t d) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = (d + 7) / 8;   // 8 warps a block, one row each
+    const int64_t cap = (int64_t)(sms > 0 ? sms : 1) * 16;
+    return (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+cudaError_t launch_ti_rows(const float *C, int64_t ldc, int32_t d, int32_t k, uint32_t *G, uint32_t *gcnt,
+                           uint32_t *hist, cudaStream_t st) {
+    const int32_t W = ti_words(k);
+    k_ti_rows<<<row_blocks(d), 256, 0, st>>>(C, ldc, d, k, W, G, gcnt, hist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ti_scan(const uint32_t *in, int64_t n, int64_t *out, cudaStream_t st) {
+    k_ti_scan<<<1, 1024, 0, st>>>(in, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ti_mtab(const uint32_t *hist, const int32_t *list, int32_t n, int32_t k, int L, const TiThr &thr,
+                           uint8_t *mtab, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_ti_mtab<<<n, TI_NB, 0, st>>>(hist, list, k, L, thr, mtab);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ti_fill(const float *C, int64_t ldc, int32_t d, int32_t k, const uint32_t *G, const uint8_t *mtab,
+                           int L, const int64_t *gptr, int64_t nzC, uint32_t *P, uint32_t *pbe, cudaStream_t st) {
+    k_ti_fill<<<row_blocks(d), 256, 0, st>>>(C, ldc, d, k, ti_words(k), G, mtab, L, gptr, nzC, P, pbe);
+    return cudaGetLastError();
+}
+
+size_t ti_query_smem(int32_t k) { return (size_t)TI_WARPS * ti_warp_words(ti_words(k)) * sizeof(uint32_t); }
+
+cudaError_t launch_ti_query(const TiQueryArgs &a, cudaStream_t st) {
+    if (a.n_list <= 0) return cudaSuccess;
+    const size_t smem = ti_query_smem(a.k);
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(k_ti_query, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ti_query, TI_WARPS * 32, smem);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t want = (a.n_list + TI_WARPS - 1) / TI_WARPS;
+    const int64_t cap = (int64_t)sms * per_sm * 4;
+    k_ti_query<<<(unsigned)(want < cap ? want : cap), TI_WARPS * 32, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace skm

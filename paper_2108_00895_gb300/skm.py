@@ -28,7 +28,8 @@ SKM_OK, SKM_ERR_INVALID, SKM_ERR_OOM, SKM_ERR_BUDGET, SKM_ERR_CUDA, SKM_ERR_STAT
 STATUS_NAMES = {0: "SKM_OK", 1: "SKM_ERR_INVALID", 2: "SKM_ERR_OOM", 3: "SKM_ERR_BUDGET",
                 4: "SKM_ERR_CUDA", 5: "SKM_ERR_STATE", 6: "SKM_ERR_TIMEOUT"}
 SKM_FP32, SKM_BF16 = 0, 1
-SKM_PRUNE_NONE, SKM_PRUNE_NCC = 0, 1
+SKM_PRUNE_NONE, SKM_PRUNE_NCC, SKM_PRUNE_NCC_INDEX = 0, 1, 2
+PRUNE_MODES = {"none": SKM_PRUNE_NONE, "ncc": SKM_PRUNE_NCC, "ncc_index": SKM_PRUNE_NCC_INDEX}
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -41,7 +42,9 @@ class skm_config(ctypes.Structure):
                 ("mem_budget", ctypes.c_size_t), ("device", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_user", ctypes.c_void_p), ("timing", ctypes.c_int32),
-                ("sparse_div", ctypes.c_int32)]
+                ("sparse_div", ctypes.c_int32), ("index_levels", ctypes.c_int32),
+                ("index_lambda", ctypes.c_double * 4), ("index_min_changed", ctypes.c_int32),
+                ("index_max_cands", ctypes.c_int32)]
 
 
 class skm_csr(ctypes.Structure):
@@ -59,7 +62,9 @@ class skm_stats(ctypes.Structure):
                 ("ms_update", ctypes.c_double), ("launches_score", ctypes.c_int64),
                 ("launches_total", ctypes.c_int64), ("fmas_exec", ctypes.c_int64),
                 ("ms_index", ctypes.c_double), ("sparse_rows", ctypes.c_int64),
-                ("sparse_entries", ctypes.c_int64)]
+                ("sparse_entries", ctypes.c_int64), ("index_docs", ctypes.c_int64),
+                ("index_sims", ctypes.c_int64), ("index_entries", ctypes.c_int64),
+                ("index_products", ctypes.c_int64), ("ms_query", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -121,7 +126,8 @@ EXPORTS = ("skm_config_default", "skm_create", "skm_destroy", "skm_last_error", 
            "skm_assign", "skm_update", "skm_set_centroids", "skm_get_centroids", "skm_n_terms",
            "skm_get_stats", "skm_mem_used", "skm_fit_batched", "skm_server_create", "skm_server_submit_assign",
            "skm_server_submit_fit", "skm_server_wait", "skm_server_release", "skm_server_get_stats",
-           "skm_server_destroy", "skm_assign_fixed_scratch", "skm_init_kmeanspp")
+           "skm_server_destroy", "skm_assign_fixed_scratch", "skm_init_kmeanspp",
+           "skm_index_candidates")
 
 # skm_assign_fixed_scratch: capacity of its fixed scratch, in (document x 256-column slice) units
 FIXED_SCRATCH_SLICE = 256
@@ -151,6 +157,7 @@ def load(build_if_missing: bool = True):
             "skm_assign": (st, [P, ctypes.POINTER(skm_csr), P, P]),
             "skm_update": (st, [P, ctypes.POINTER(skm_csr), P, P]),
             "skm_init_kmeanspp": (st, [P, ctypes.POINTER(skm_csr), P, P]),
+            "skm_index_candidates": (st, [P, ctypes.POINTER(skm_csr), ctypes.c_int32, P]),
             "skm_set_centroids": (st, [P, ctypes.c_int32, P, ctypes.c_int32]),
             "skm_get_centroids": (st, [P, P, ctypes.c_int32]),
             "skm_n_terms": (ctypes.c_int32, [P]),
@@ -261,6 +268,10 @@ def skm_fit(ctx, csr: skm_csr, init_ids, assign_out, objective_out=None, iters_o
 
 def skm_init_kmeanspp(ctx, csr: skm_csr, uniforms, ids_out) -> None:
     _check(ctx, load().skm_init_kmeanspp(ctx, ctypes.byref(csr), _ptr(uniforms), _ptr(ids_out)))
+
+
+def skm_index_candidates(ctx, csr: skm_csr, level: int, bits) -> None:
+    _check(ctx, load().skm_index_candidates(ctx, ctypes.byref(csr), int(level), _ptr(bits)))
 
 
 def skm_assign(ctx, csr: skm_csr, assign_out, score_out=None) -> None:
@@ -380,8 +391,11 @@ class FitResult:
 class SphericalKMeans:
     """One libskm context: exact spherical k-means on one GPU.
 
-    precision: "fp32" or "bf16" (scored centroid copy); prune: "none" or "ncc"
-    (Sec. 3.1 skip); rescore: FP64 rescoring of near ties; tau: margin threshold;
+    precision: "fp32" or "bf16" (scored centroid copy); prune: "none", "ncc" (Sec. 3.1
+    skip) or "ncc_index" (plus the threshold index of Sec. 3.2, with the minimum dot
+    products index_lambdas, used in steps after more than index_min_changed centroids
+    changed; -1 = every step; documents with more than index_max_cands candidates, 0 =
+    automatic, are scored densely); rescore: FP64 rescoring of near ties; tau: margin threshold;
     sparse_div: centroid rows with at most k / sparse_div nonzeros are scored from their
     nonzero lists (0 = off; results are identical either way).
     """
@@ -389,11 +403,22 @@ class SphericalKMeans:
     def __init__(self, k: int, precision: str = "fp32", prune: str = "none", max_iter: int = 20,
                  shift_tol: float = -1.0, rescore: bool = True, tau: float = 0.0, device: int = 0,
                  stream: int | None = None, mem_budget: int = 0, timing: bool = False,
-                 allocator: str = "torch", sparse_div: int = 0):
+                 allocator: str = "torch", sparse_div: int = 0, index_lambdas=None,
+                 index_min_changed: int | None = None, index_max_cands: int = 0):
         self.lib = load()
         cfg = skm_config_default(k)
         cfg.precision = {"fp32": SKM_FP32, "bf16": SKM_BF16}[precision]
-        cfg.prune = {"none": SKM_PRUNE_NONE, "ncc": SKM_PRUNE_NCC}[prune]
+        cfg.prune = PRUNE_MODES[prune]
+        if index_lambdas is not None:
+            lam = [float(x) for x in index_lambdas]
+            if not 1 <= len(lam) <= 4:
+                raise ValueError("1 to 4 index thresholds")
+            cfg.index_levels = len(lam)
+            for q, v in enumerate(lam):
+                cfg.index_lambda[q] = v
+        if index_min_changed is not None:
+            cfg.index_min_changed = int(index_min_changed)
+        cfg.index_max_cands = int(index_max_cands)
         cfg.max_iter = int(max_iter)
         cfg.shift_tol = float(shift_tol)
         cfg.rescore = int(bool(rescore))
@@ -478,6 +503,15 @@ class SphericalKMeans:
         skm_assign(self.ctx, csr, assign_out, score_out)
         return assign_out, score_out
 
+    def index_candidates(self, docs, level: int, n_terms: int | None = None) -> np.ndarray:
+        """Candidate sets of the threshold index at index_lambdas[level] for the resident
+        centroids: a bool matrix [n_docs, k] (Sec. 3.2 query, no baseline)."""
+        csr, keep, on_dev = make_csr(docs, n_terms)
+        W = (self.k + 31) // 32
+        bits = np.zeros((csr.n_docs, W), np.uint32)
+        skm_index_candidates(self.ctx, csr, level, bits)
+        return np.unpackbits(bits.view(np.uint8), axis=1, bitorder="little")[:, :self.k].astype(bool)
+
     def update(self, docs, assign, n_terms: int | None = None) -> int:
         csr, keep, on_dev = make_csr(docs, n_terms)
         a = assign if on_dev else np.ascontiguousarray(assign, dtype=np.int32)
@@ -519,7 +553,7 @@ class Server:
         cfg.max_batch_docs = int(max_batch_docs)
         cfg.max_batch_nnz = int(max_batch_nnz)
         cfg.job_precision = {"fp32": SKM_FP32, "bf16": SKM_BF16}[job_precision]
-        cfg.job_prune = {"none": SKM_PRUNE_NONE, "ncc": SKM_PRUNE_NCC}[job_prune]
+        cfg.job_prune = PRUNE_MODES[job_prune]
         cfg.rescore_tau = float(tau)
         self.resident = resident
         h = ctypes.c_void_p()
