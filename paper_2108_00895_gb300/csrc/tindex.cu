@@ -45,7 +45,8 @@ constexpr int TI_WARPS = 8;
 constexpr uint32_t TI_KEY0 = 1536;   // float bits >> 19 of 2^-31, the lowest bin's lower edge
 
 constexpr int TI_STAGE = 64;   // most nonzeros of a document the query serves
-constexpr int TI_CAND = 512;   // most candidates it scores
+constexpr int TI_CAND = 256;   // most candidates it scores
+constexpr int TI_WALK = 8;     // list entries a lane loads at a time
 
 // Shared-memory words of one query warp (layout in ti_warp_smem), a multiple of 4 words.
 __host__ __device__ constexpr int64_t ti_warp_words(int32_t W) {
@@ -194,59 +195,61 @@ __global__ void __launch_bounds__(TI_NB) k_ti_mtab(const uint32_t *hist, const i
 }
 
 // ------------------------------------------------------------------------------------
-// Build pass 3: one warp per row t, one level at a time. Reads only the nonzeros (the
-// bitmap says where), counts the level's entries per m bucket (bucket b holds m in
-// (2^(b-1), 2^b], the last one m > 64), then writes (j << 8 | m) bucket by bucket, in
-// centroid order within a bucket; pbe[(l d + t) TI_MB + b] = end of bucket b in the row's
-// list. A document of n nonzeros has counts <= n, so it walks only the buckets up to n's.
+// Build pass 3: one warp per row t. Reads only the nonzeros (the bitmap says where) in two
+// passes: the first counts each level's entries per m bucket (bucket b holds m in
+// (2^(b-1), 2^b], the last one m > 64), the second writes (j << 8 | m) bucket by bucket,
+// in centroid order within a bucket (lanes with the same bucket grouped by match_any, the
+// group's offsets kept per warp in shared memory). pbe[(l d + t) TI_MB + b] = end of
+// bucket b in the row's list. A document of n nonzeros has counts <= n, so it walks only
+// the buckets up to n's.
 // ------------------------------------------------------------------------------------
-__global__ void k_ti_fill(const float *C, int64_t ldc, int32_t d, int32_t k, int32_t W, const uint32_t *G,
-                          const uint8_t *mtab, int L, const int64_t *gptr, int64_t nzC, uint32_t *P,
-                          uint32_t *pbe) {
+constexpr int TI_FILL_WARPS = 8;
+
+__global__ void __launch_bounds__(TI_FILL_WARPS * 32) k_ti_fill(const float *C, int64_t ldc, int32_t d, int32_t k,
+                                                               int32_t W, const uint32_t *G, const uint8_t *mtab,
+                                                               int L, const int64_t *gptr, int64_t nzC, uint32_t *P,
+                                                               uint32_t *pbe) {
+    __shared__ uint32_t at_sm[TI_FILL_WARPS][TI_MAXL * TI_MB];
     const int lane = threadIdx.x & 31;
+    uint32_t *at = at_sm[threadIdx.x >> 5];
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const unsigned below = (1u << lane) - 1u;
     for (int64_t t = warp; t < d; t += nwarps) {
         const float *row = C + t * ldc;
         const int64_t base = gptr[t];
-        for (int l = 0; l < L; ++l) {
-            const uint8_t *ml = mtab + (size_t)l * k * TI_NB;
-            uint32_t cnt[TI_MB];
-#pragma unroll
-            for (int b = 0; b < TI_MB; ++b) cnt[b] = 0u;
+        if (lane < TI_MAXL * TI_MB) at[lane] = 0u;
+        __syncwarp();
+        for (int pass = 0; pass < 2; ++pass) {
             for (int w = 0; w < W; ++w) {
                 const uint32_t g = __ldg(G + t * W + w);
                 if (g == 0u) continue;
                 const int j = w * 32 + lane;
                 const bool nz = (g >> lane) & 1u;
-                const uint32_t m = nz ? (uint32_t)__ldg(ml + (size_t)j * TI_NB + ti_bin(__ldg(row + j))) : 0u;
-                const int bid = m ? ti_mbucket(m) : -1;
-#pragma unroll
-                for (int b = 0; b < TI_MB; ++b) cnt[b] += __popc(__ballot_sync(FULL, bid == b));
-            }
-            uint32_t at[TI_MB];
-            uint32_t run = 0u;
-#pragma unroll
-            for (int b = 0; b < TI_MB; ++b) {
-                at[b] = run;
-                run += cnt[b];
-                if (lane == b) pbe[((int64_t)l * d + t) * TI_MB + b] = run;
-            }
-            uint32_t *Pl = P + (int64_t)l * nzC + base;
-            for (int w = 0; w < W; ++w) {
-                const uint32_t g = __ldg(G + t * W + w);
-                if (g == 0u) continue;
-                const int j = w * 32 + lane;
-                const bool nz = (g >> lane) & 1u;
-                const uint32_t m = nz ? (uint32_t)__ldg(ml + (size_t)j * TI_NB + ti_bin(__ldg(row + j))) : 0u;
-                const int bid = m ? ti_mbucket(m) : -1;
-#pragma unroll
-                for (int b = 0; b < TI_MB; ++b) {
-                    const unsigned bal = __ballot_sync(FULL, bid == b);
-                    if (bid == b) Pl[at[b] + __popc(bal & below)] = ((uint32_t)j << 8) | m;
-                    at[b] += __popc(bal);
+                const int bin = nz ? ti_bin(__ldg(row + j)) : 0;
+                for (int l = 0; l < L; ++l) {
+                    const uint32_t m = nz ? (uint32_t)__ldg(mtab + ((size_t)l * k + j) * TI_NB + bin) : 0u;
+                    const int key = m ? ti_mbucket(m) : -1;
+                    const unsigned grp = __match_any_sync(FULL, key);
+                    const bool lead = key >= 0 && lane == __ffs(grp) - 1;
+                    if (pass == 1 && key >= 0)
+                        P[(int64_t)l * nzC + base + at[l * TI_MB + key] + __popc(grp & below)] = ((uint32_t)j << 8) | m;
+                    __syncwarp();
+                    if (lead) at[l * TI_MB + key] += __popc(grp);
+                    __syncwarp();
                 }
+            }
+            if (pass == 0) {
+                // counts -> bucket starts; the ends go to pbe
+                uint32_t start = 0u;
+                if (lane < L * TI_MB) {
+                    const int l = lane / TI_MB, b = lane % TI_MB;
+                    for (int q = 0; q < b; ++q) start += at[l * TI_MB + q];
+                    pbe[((int64_t)l * d + t) * TI_MB + b] = start + at[lane];
+                }
+                __syncwarp();
+                if (lane < TI_MAXL * TI_MB) at[lane] = start;
+                __syncwarp();
             }
         }
     }
@@ -255,8 +258,8 @@ __global__ void k_ti_fill(const float *C, int64_t ldc, int32_t d, int32_t k, int
 // ------------------------------------------------------------------------------------
 // Query: one warp per listed document (grid-stride). A document of at most TI_STAGE
 // nonzeros is staged in shared memory, and every phase issues its loads in independent
-// batches (the baseline's entries, the bitmap words of 8 terms at a time, 4 list entries
-// at a time, a candidate's entries for 8 terms at a time), so that a warp waits for a
+// batches (the baseline's entries, the bitmap words of 4 words x 8 terms at a time, 8 list
+// entries at a time, a candidate's entries for 8 terms at a time), so that a warp waits for a
 // few memory round trips per document rather than one per term.
 // Shared memory per warp (32-bit words): the staged terms, values and baseline entries,
 // the list offsets (64-bit), lengths and prefix sums; the 8 count planes of each bitmap
@@ -320,6 +323,15 @@ __global__ void __launch_bounds__(TI_WARPS * 32) k_ti_query(TiQueryArgs a) {
     const int W = a.W;
     const TiWarpSmem sm = ti_warp_smem(ti_sm + (size_t)wib * ti_warp_words(W), W);
     __shared__ int ncand[TI_WARPS];
+    // changed centroids as a bitmap shared by the block's warps (the Sec. 3.1 filter)
+    uint32_t *chg = ti_sm + (size_t)TI_WARPS * ti_warp_words(W);
+    if (a.ncc && a.changed)
+        for (int w = threadIdx.x; w < W; w += blockDim.x) {
+            uint32_t bits = 0u;
+            for (int b = 0; b < 32 && w * 32 + b < a.k; ++b) bits |= (a.changed[w * 32 + b] ? 1u : 0u) << b;
+            chg[w] = bits;
+        }
+    __syncthreads();
     unsigned long long n_docs = 0, n_sims = 0, n_walk = 0, n_prod = 0;
     const int64_t nw = (int64_t)gridDim.x * TI_WARPS;
     const int cand_cap = a.max_cands > 0 ? min(TI_CAND, a.max_cands) : min(TI_CAND, (int)((int64_t)a.k * a.elt / 32));
@@ -379,30 +391,47 @@ __global__ void __launch_bounds__(TI_WARPS * 32) k_ti_query(TiQueryArgs a) {
             sm.len[p] = __ldg(pbe + (int64_t)t * TI_MB);
         }
         // overlap counts: bit-sliced 8-bit counters (ripple-carry adds; nnz <= 64 < 256),
-        // lane-owned words, bitmap words of 8 terms loaded at a time
-        for (int w = lane; w < W; w += 32) {
-            uint32_t c[TI_PLANES];
+        // lane-owned words in groups of 4, kept in shared memory between term batches of 8;
+        // a group's 32 bitmap words are loaded before any is added
+        for (int w0 = lane; w0 < W; w0 += 32 * 4) {
+            for (int u = 0; u < 4; ++u) {
+                const int w = w0 + 32 * u;
+                if (w < W) {
 #pragma unroll
-            for (int q = 0; q < TI_PLANES; ++q) c[q] = 0u;
-            for (int p0 = 0; p0 < nnz; p0 += 8) {
-                uint32_t g[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    g[u] = p0 + u < nnz ? __ldg(a.G + (int64_t)sm.t[p0 + u] * W + w) : 0u;
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    uint32_t cy = g[u];
-#pragma unroll
-                    for (int q = 0; q < TI_PLANES; ++q) {
-                        const uint32_t nq = c[q] ^ cy;
-                        cy &= c[q];
-                        c[q] = nq;
-                    }
+                    for (int q = 0; q < TI_PLANES; ++q) sm.pl[TI_PLANES * w + q] = 0u;
+                    sm.cb[w] = 0u;
                 }
             }
+            for (int p0 = 0; p0 < nnz; p0 += 8) {
+                uint32_t g[4][8];
 #pragma unroll
-            for (int q = 0; q < TI_PLANES; ++q) sm.pl[TI_PLANES * w + q] = c[q];
-            sm.cb[w] = 0u;
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 8; ++v) {
+                        const int w = w0 + 32 * u;
+                        g[u][v] = (w < W && p0 + v < nnz) ? __ldg(a.G + (int64_t)sm.t[p0 + v] * W + w) : 0u;
+                    }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int w = w0 + 32 * u;
+                    if (w >= W) break;
+                    uint32_t c[TI_PLANES];
+#pragma unroll
+                    for (int q = 0; q < TI_PLANES; ++q) c[q] = sm.pl[TI_PLANES * w + q];
+#pragma unroll
+                    for (int v = 0; v < 8; ++v) {
+                        uint32_t cy = g[u][v];
+#pragma unroll
+                        for (int q = 0; q < TI_PLANES; ++q) {
+                            const uint32_t nq = c[q] ^ cy;
+                            cy &= c[q];
+                            c[q] = nq;
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < TI_PLANES; ++q) sm.pl[TI_PLANES * w + q] = c[q];
+                }
+            }
         }
         __syncwarp();
         if (lane == 0) {
@@ -420,10 +449,10 @@ __global__ void __launch_bounds__(TI_WARPS * 32) k_ti_query(TiQueryArgs a) {
         const uint32_t *Pl = a.P + (int64_t)lev * a.nzC;
         const bool nccf = a.ncc && a0 >= 0 && !a.changed[a0];
         int pc = 0;   // this lane's term: the last p with pre[p] <= q (q only grows)
-        for (uint32_t q0 = lane; q0 < E; q0 += 32 * 4) {
-            uint32_t pe[4];
+        for (uint32_t q0 = lane; q0 < E; q0 += 32 * TI_WALK) {
+            uint32_t pe[TI_WALK];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < TI_WALK; ++u) {
                 const uint32_t q = q0 + 32u * u;
                 pe[u] = 0u;
                 if (q < E) {
@@ -432,18 +461,24 @@ __global__ void __launch_bounds__(TI_WARPS * 32) k_ti_query(TiQueryArgs a) {
                 }
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < TI_WALK; ++u) {
                 if (q0 + 32u * u >= E) break;
                 const int j = (int)(pe[u] >> 8);
                 const uint32_t m = pe[u] & 255u;
                 const int w = j >> 5, b = j & 31;
-                const uint4 lo4 = *reinterpret_cast<const uint4 *>(sm.pl + TI_PLANES * w);
-                const uint4 hi4 = *reinterpret_cast<const uint4 *>(sm.pl + TI_PLANES * w + 4);
-                const uint32_t c = ((lo4.x >> b) & 1u) | (((lo4.y >> b) & 1u) << 1) | (((lo4.z >> b) & 1u) << 2) |
-                                   (((lo4.w >> b) & 1u) << 3) | (((hi4.x >> b) & 1u) << 4) |
-                                   (((hi4.y >> b) & 1u) << 5) | (((hi4.z >> b) & 1u) << 6) |
-                                   (((hi4.w >> b) & 1u) << 7);
-                if (c >= m && j != a0 && (!nccf || a.changed[j])) atomicOr(sm.cb + w, 1u << b);
+                if (j == a0 || (nccf && !((chg[w] >> b) & 1u))) continue;
+                // the document holds the entry's term, so its count is at least 1
+                bool take = m <= 1u;
+                if (!take) {
+                    const uint4 lo4 = *reinterpret_cast<const uint4 *>(sm.pl + TI_PLANES * w);
+                    const uint4 hi4 = *reinterpret_cast<const uint4 *>(sm.pl + TI_PLANES * w + 4);
+                    const uint32_t c = ((lo4.x >> b) & 1u) | (((lo4.y >> b) & 1u) << 1) |
+                                       (((lo4.z >> b) & 1u) << 2) | (((lo4.w >> b) & 1u) << 3) |
+                                       (((hi4.x >> b) & 1u) << 4) | (((hi4.y >> b) & 1u) << 5) |
+                                       (((hi4.z >> b) & 1u) << 6) | (((hi4.w >> b) & 1u) << 7);
+                    take = c >= m;
+                }
+                if (take) atomicOr(sm.cb + w, 1u << b);
             }
         }
         __syncwarp();
@@ -566,11 +601,14 @@ cudaError_t launch_ti_mtab(const uint32_t *hist, const int32_t *list, int32_t n,
 
 cudaError_t launch_ti_fill(const float *C, int64_t ldc, int32_t d, int32_t k, const uint32_t *G, const uint8_t *mtab,
                            int L, const int64_t *gptr, int64_t nzC, uint32_t *P, uint32_t *pbe, cudaStream_t st) {
-    k_ti_fill<<<row_blocks(d), 256, 0, st>>>(C, ldc, d, k, ti_words(k), G, mtab, L, gptr, nzC, P, pbe);
+    k_ti_fill<<<row_blocks(d), TI_FILL_WARPS * 32, 0, st>>>(C, ldc, d, k, ti_words(k), G, mtab, L, gptr, nzC, P, pbe);
     return cudaGetLastError();
 }
 
-size_t ti_query_smem(int32_t k) { return (size_t)TI_WARPS * ti_warp_words(ti_words(k)) * sizeof(uint32_t); }
+size_t ti_query_smem(int32_t k) {
+    const int32_t W = ti_words(k);
+    return ((size_t)TI_WARPS * ti_warp_words(W) + (size_t)W) * sizeof(uint32_t);
+}
 
 cudaError_t launch_ti_query(const TiQueryArgs &a, cudaStream_t st) {
     if (a.n_list <= 0) return cudaSuccess;
