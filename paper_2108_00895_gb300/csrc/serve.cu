@@ -75,7 +75,7 @@ struct skm_server {
 namespace {
 
 // Device memory a clustering job may hold (mirrors the context's allocations, rounded up).
-size_t fit_estimate(const skm_csr &d, int32_t k, int precision) {
+size_t fit_estimate(const skm_csr &d, int32_t k, int precision, int prune) {
     const size_t n = (size_t)d.n_docs, e = (size_t)d.nnz, t = (size_t)d.n_terms;
     const int slice = precision == SKM_BF16 ? (k <= 256 ? 256 : 512) : (k <= 128 ? 128 : 256);
     const size_t ldc = ((size_t)k + slice - 1) / slice * slice;
@@ -89,7 +89,14 @@ size_t fit_estimate(const skm_csr &d, int32_t k, int precision) {
     // df_t nonzeros, so each holds at most nnz entries; plus the marked column stream
     const size_t esz = precision == SKM_BF16 ? 4 : 8;
     const size_t sparse = e * (4 + 2 * esz) + t * (9 + 2 * (slices + 1) * 4);
-    return (cent + docs + post + per_doc + per_clus + sparse) * 11 / 10 + (size_t(64) << 20);
+    // threshold index (NCC+INDEX): bitmap, per-term offsets and bucket ends, value bins and
+    // bounds, and 4 lists of at most nnz entries (a centroid's nonzeros are its members' terms)
+    const size_t words = ((size_t)k + 31) / 32;
+    const size_t tindex = prune == SKM_PRUNE_NCC_INDEX
+                              ? t * (words * 4 + 12 + 4 * 8 * 4) + (size_t)k * 512 * (4 + 4) + 4 * e * 4 +
+                                    (size_t)k * 8
+                              : 0;
+    return (cent + docs + post + per_doc + per_clus + sparse + tindex) * 11 / 10 + (size_t(64) << 20);
 }
 
 void assign_worker(skm_server *S) {
@@ -327,7 +334,7 @@ SKM_API skm_status skm_server_submit_fit(skm_server *S, const skm_csr *docs, int
     r->k = k;
     r->max_iter = max_iter;
     r->init.assign(init_doc_ids, init_doc_ids + k);
-    r->mem_est = fit_estimate(*docs, k, S->cfg.job_precision);
+    r->mem_est = fit_estimate(*docs, k, S->cfg.job_precision, S->cfg.job_prune);
     return submit(S, r, ticket);
 }
 
