@@ -90,8 +90,11 @@ struct skm_ctx {
     // k-means++ seeding
     Buf pp_dist, pp_w, pp_csum, pp_drawn, pp_seed, pp_ids, pp_u;
     // threshold index of Sec. 3.2 (tindex.cu), built for centroid epoch ti_epoch
-    Buf ti_G, ti_gcnt, ti_gptr, ti_hist, ti_mtab, ti_P, ti_pbe, ti_stats, ti_dump;
+    Buf ti_G, ti_gcnt, ti_gptr, ti_hist, ti_mtab, ti_P, ti_pbe, ti_stats, ti_dump, ti_scan;
     int64_t ti_epoch = 0, ti_nzC = 0;
+    // G and the value bins describe the centroids of epoch ti_maint_epoch; the update keeps
+    // them current (clearing and setting the bits and counts of the entries it rewrites)
+    int64_t ti_maint_epoch = -1;
 
     skm_stats stats{};
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_score, ev_decide, ev_update, ev_index, ev_query;
@@ -574,22 +577,33 @@ const SparseArgs *apply_rare(skm_ctx *ctx, const RareView &rv, ScoreArgs &sa, Sp
 
 // Scoring pass over a document list (nullable = all) against all k or the moved list,
 // followed by the decision kernel.
+// The threshold index's bitmap and value bins match the resident centroids.
+bool ti_current(const skm_ctx *ctx) { return ctx->ti_G.p && ctx->ti_maint_epoch == ctx->cent_epoch; }
+
 // Threshold index (Sec. 3.2) of the resident FP32 master, rebuilt when the centroids changed.
 skm_status build_tindex(skm_ctx *ctx) {
     if (ctx->ti_epoch == ctx->cent_epoch) return SKM_OK;
     const int32_t k = ctx->cfg.k, d = ctx->d, W = ti_words(k);
     const int L = ctx->cfg.index_levels;
     Timed tm(ctx, ctx->ev_index);
-    SKM_TRY(ensure(ctx, ctx->ti_G, sizeof(uint32_t) * (size_t)d * W));
+    const size_t g_bytes = sizeof(uint32_t) * (size_t)d * W;
+    const bool incremental = ti_current(ctx) && ctx->ti_G.bytes >= g_bytes;
+    SKM_TRY(ensure(ctx, ctx->ti_G, g_bytes));
     SKM_TRY(ensure(ctx, ctx->ti_gcnt, sizeof(uint32_t) * (size_t)d));
     SKM_TRY(ensure(ctx, ctx->ti_gptr, sizeof(int64_t) * ((size_t)d + 1)));
     SKM_TRY(ensure(ctx, ctx->ti_hist, sizeof(uint32_t) * (size_t)k * TI_NB));
     SKM_TRY(ensure(ctx, ctx->ti_mtab, (size_t)L * k * TI_NB));
     SKM_TRY(ensure(ctx, ctx->ti_pbe, sizeof(uint32_t) * (size_t)L * d * TI_MB));
-    SKM_CUDA(cudaMemsetAsync(ctx->ti_hist.p, 0, sizeof(uint32_t) * (size_t)k * TI_NB, ctx->st));
-    SKM_CUDA(launch_ti_rows(P<float>(ctx->C32), ctx->ldc, d, k, P<uint32_t>(ctx->ti_G), P<uint32_t>(ctx->ti_gcnt),
-                            P<uint32_t>(ctx->ti_hist), ctx->st));
-    SKM_CUDA(launch_ti_scan(P<uint32_t>(ctx->ti_gcnt), d, P<int64_t>(ctx->ti_gptr), ctx->st));
+    if (incremental) {
+        // the update kept G and the bins current: only the row counts are recounted
+        SKM_CUDA(launch_ti_gcnt(P<uint32_t>(ctx->ti_G), d, W, P<uint32_t>(ctx->ti_gcnt), ctx->st));
+    } else {
+        SKM_CUDA(cudaMemsetAsync(ctx->ti_hist.p, 0, sizeof(uint32_t) * (size_t)k * TI_NB, ctx->st));
+        SKM_CUDA(launch_ti_rows(P<float>(ctx->C32), ctx->ldc, d, k, P<uint32_t>(ctx->ti_G),
+                                P<uint32_t>(ctx->ti_gcnt), P<uint32_t>(ctx->ti_hist), ctx->st));
+    }
+    SKM_TRY(ensure(ctx, ctx->ti_scan, ti_scan_scratch(d)));
+    SKM_CUDA(launch_ti_scan(P<uint32_t>(ctx->ti_gcnt), d, P<int64_t>(ctx->ti_gptr), P<int64_t>(ctx->ti_scan), ctx->st));
     TiThr thr{};
     for (int l = 0; l < L; ++l) thr.v[l] = ctx->cfg.index_lambda[l] * ctx->cfg.index_lambda[l] * (1.0 - 1e-9);
     SKM_CUDA(launch_ti_mtab(P<uint32_t>(ctx->ti_hist), nullptr, k, k, L, thr, P<uint8_t>(ctx->ti_mtab), ctx->st));
@@ -603,6 +617,7 @@ skm_status build_tindex(skm_ctx *ctx) {
                             ctx->st));
     ctx->stats.launches_total += 4;
     ctx->ti_epoch = ctx->cent_epoch;
+    ctx->ti_maint_epoch = ctx->cent_epoch;
     return SKM_OK;
 }
 
@@ -792,6 +807,8 @@ skm_status rescore_queues(skm_ctx *ctx, const DevCsr &dc, int32_t *a_new, float 
 // (and for unknown supports) whole columns are cleared.
 skm_status clear_recomputed(skm_ctx *ctx, const DevCsr &dc, const Postings &pg, const int32_t *a_old, bool sparse) {
     const int32_t k = ctx->cfg.k;
+    uint32_t *tiG = ti_current(ctx) ? P<uint32_t>(ctx->ti_G) : nullptr;
+    const int32_t tiW = ti_words(k);
     float *C32 = P<float>(ctx->C32);
     __nv_bfloat16 *C16 = ctx->cfg.precision == SKM_BF16 ? P<__nv_bfloat16>(ctx->C16) : nullptr;
     ctx->h_changed.resize(k);
@@ -825,14 +842,14 @@ skm_status clear_recomputed(skm_ctx *ctx, const DevCsr &dc, const Postings &pg, 
     if (n_members > 0 && sparse) {
         SKM_CUDA(cudaMemcpyAsync(ctx->zflag.p, ctx->h_flag.data(), k, cudaMemcpyHostToDevice, ctx->st));
         SKM_CUDA(launch_zero_members(P<int32_t>(ctx->row_idx), P<int32_t>(ctx->pterm), dc.nnz, a_old,
-                                     P<uint8_t>(ctx->zflag), C32, C16, ctx->ldc, ctx->st));
+                                     P<uint8_t>(ctx->zflag), C32, C16, ctx->ldc, tiG, tiW, ctx->st));
         ctx->stats.launches_total++;
     }
     if (!seeds.empty()) {
         SKM_CUDA(cudaMemcpyAsync(ctx->zlist.p, seeds.data(), sizeof(int32_t) * seeds.size(), cudaMemcpyHostToDevice,
                                  ctx->st));
         SKM_CUDA(launch_zero_seeds(P<int32_t>(ctx->zlist), (int32_t)seeds.size(), P<int32_t>(ctx->init_ids),
-                                   dc.row_ptr, dc.col, C32, C16, ctx->ldc, ctx->st));
+                                   dc.row_ptr, dc.col, C32, C16, ctx->ldc, tiG, tiW, ctx->st));
         ctx->stats.launches_total++;
         SKM_TRY(sync(ctx));   // zlist is reused below
     }
@@ -840,7 +857,7 @@ skm_status clear_recomputed(skm_ctx *ctx, const DevCsr &dc, const Postings &pg, 
         SKM_CUDA(cudaMemcpyAsync(ctx->zlist.p, ctx->h_list.data(), sizeof(int32_t) * ctx->h_list.size(),
                                  cudaMemcpyHostToDevice, ctx->st));
         SKM_CUDA(launch_zero_cols(P<int32_t>(ctx->zlist), (int32_t)ctx->h_list.size(), ctx->d, C32, C16, ctx->ldc,
-                                  ctx->st));
+                                  tiG, tiW, ctx->st));
         ctx->stats.launches_total++;
     }
     // supports after this update: recomputed -> its new members; a changed cluster left
@@ -913,6 +930,12 @@ skm_status update_step(skm_ctx *ctx, const DevCsr &dc, const Postings &pg, const
         u.CM = build_cm ? ctx->CM.p : nullptr;
         u.precision = ctx->cfg.precision;
         u.ldc = ctx->ldc;
+        const bool ti_keep = ti_current(ctx);
+        if (ti_keep) {
+            u.tiG = P<uint32_t>(ctx->ti_G);
+            u.tiHist = P<uint32_t>(ctx->ti_hist);
+            u.tiW = ti_words(k);
+        }
         SKM_CUDA(cudaMemsetAsync(u.normsq128, 0, 2 * sizeof(unsigned long long) * n_moved, ctx->st));
         SKM_CUDA(cudaMemsetAsync(u.sq128, 0, 2 * sizeof(unsigned long long) * n_moved, ctx->st));
         SKM_CUDA(launch_update_norm(u, ctx->st));
@@ -923,10 +946,12 @@ skm_status update_step(skm_ctx *ctx, const DevCsr &dc, const Postings &pg, const
             SKM_CUDA(launch_cm_moved(u.moved, P<int32_t>(ctx->sizes), n_moved, ctx->d, u.C32, u.CM, u.precision,
                                      u.ldc, ctx->st));
         ctx->cm_valid = build_cm;
+        if (ti_keep) SKM_CUDA(launch_ti_zero_hist(u.moved, P<int32_t>(ctx->sizes), n_moved, u.tiHist, ctx->st));
         SKM_CUDA(launch_update_write(u, ctx->st));
         SKM_CUDA(launch_from_u128(nullptr, u.sq128, n_moved, pg.F, nullptr, nullptr, P<double>(ctx->newsq), ctx->st));
         ctx->stats.launches_total += 8;
         ctx->cent_epoch++;
+        if (ti_keep) ctx->ti_maint_epoch = ctx->cent_epoch;
     }
     // with no moved cluster pos_in_m is -1 everywhere and the objective is sum_j ||S_j||
     SKM_CUDA(launch_finish(P<int32_t>(ctx->pos_in_m), P<int32_t>(ctx->sizes), k,
@@ -1023,7 +1048,7 @@ skm_status skm_destroy(skm_ctx *ctx) {
                   &ctx->colm, &ctx->skipped, &ctx->zflag, &ctx->zlist, &ctx->pp_dist, &ctx->pp_w, &ctx->pp_csum,
                   &ctx->pp_drawn, &ctx->pp_seed, &ctx->pp_ids, &ctx->pp_u, &ctx->ti_G, &ctx->ti_gcnt,
                   &ctx->ti_gptr, &ctx->ti_hist, &ctx->ti_mtab, &ctx->ti_P, &ctx->ti_pbe, &ctx->ti_stats,
-                  &ctx->ti_dump,
+                  &ctx->ti_dump, &ctx->ti_scan,
                   &ctx->normsq128, &ctx->sq128, &ctx->sq_store, &ctx->counters, &ctx->counters64, &ctx->scal,
                   &ctx->obj, &ctx->init_ids};
     for (Buf *b : all) release(ctx, *b);

@@ -153,6 +153,9 @@ struct UpdateArgs {
     float *C32;
     __nv_bfloat16 *C16;        // nullable (FP32 mode)
     void *CM;                  // nullable: compacted moved matrix (precision of the scored copy)
+    uint32_t *tiG;             // nullable: threshold-index bitmap to keep current (bits set
+    uint32_t *tiHist;          //   for written nonzeros) and bin counts (one per nonzero)
+    int32_t tiW;
     int precision;
     int64_t ldc;
 };
@@ -166,12 +169,16 @@ cudaError_t launch_from_u128(const unsigned long long *normsq128, const unsigned
 // Clearing recomputed columns before the write pass (see update.cu): by the postings of the
 // flagged clusters' old members, by the seed documents of listed clusters, or all rows of
 // listed columns; and the compacted moved matrix (cleared or kept-centroid columns).
+// tiG (nullable): threshold-index bitmap with W words a row, whose bits of the cleared
+// entries are cleared too.
 cudaError_t launch_zero_members(const int32_t *row_idx, const int32_t *pterm, int64_t nnz, const int32_t *a_old,
-                                const uint8_t *flag, float *C32, __nv_bfloat16 *C16, int64_t ldc, cudaStream_t st);
+                                const uint8_t *flag, float *C32, __nv_bfloat16 *C16, int64_t ldc, uint32_t *tiG,
+                                int32_t W, cudaStream_t st);
 cudaError_t launch_zero_seeds(const int32_t *list, int32_t n, const int32_t *init_ids, const int64_t *row_ptr,
-                              const int32_t *col, float *C32, __nv_bfloat16 *C16, int64_t ldc, cudaStream_t st);
+                              const int32_t *col, float *C32, __nv_bfloat16 *C16, int64_t ldc, uint32_t *tiG,
+                              int32_t W, cudaStream_t st);
 cudaError_t launch_zero_cols(const int32_t *list, int32_t n, int32_t d, float *C32, __nv_bfloat16 *C16, int64_t ldc,
-                             cudaStream_t st);
+                             uint32_t *tiG, int32_t W, cudaStream_t st);
 cudaError_t launch_cm_moved(const int32_t *moved, const int32_t *sizes, int32_t n_moved, int32_t d, const float *C32,
                             void *CM, int precision, int64_t ldc, cudaStream_t st);
 cudaError_t launch_mdoc(const int32_t *a, const int32_t *pos_in_m, int64_t n, int32_t *mdoc,
@@ -194,6 +201,15 @@ constexpr int TI_MB = 8;       // m buckets of each term's list
 constexpr int TI_PLANES = 8;   // bits of the overlap counts and of the stored m bounds
 constexpr int32_t TI_MAX_K = 16384;
 __host__ __device__ constexpr int32_t ti_words(int32_t k) { return (k + 31) / 32; }
+
+constexpr uint32_t TI_KEY0 = 1536;   // float bits >> 19 of 2^-31, the lowest bin's lower edge
+
+// Value bin of an entry: 16 bins per octave of |v| (the float bits >> 19), everything below
+// 2^-31 in bin 0, everything from 1.9375 up in the last (open) bin.
+__device__ __forceinline__ int ti_bin(float v) {
+    const int key = (int)(__float_as_uint(fabsf(v)) >> 19) - (int)TI_KEY0;
+    return key < 0 ? 0 : (key > TI_NB - 1 ? TI_NB - 1 : key);
+}
 
 struct TiThr {
     double v[TI_MAXL];   // lambda_l^2 (1 - 1e-9)
@@ -237,11 +253,18 @@ struct TiQueryArgs {
     unsigned long long *stats;  // nullable: [documents, similarities, P entries walked, products]
 };
 
+// Row counts of the bitmap G (popcount of each row's words).
+cudaError_t launch_ti_gcnt(const uint32_t *G, int32_t d, int32_t W, uint32_t *gcnt, cudaStream_t st);
+// Zero the bin counts of the recomputed centroids of the moved list (sizes[j] > 0).
+cudaError_t launch_ti_zero_hist(const int32_t *moved, const int32_t *sizes, int32_t n_moved, uint32_t *hist,
+                                cudaStream_t st);
 // G, row counts and bin counts of every centroid (hist zeroed by the caller).
 cudaError_t launch_ti_rows(const float *C, int64_t ldc, int32_t d, int32_t k, uint32_t *G, uint32_t *gcnt,
                            uint32_t *hist, cudaStream_t st);
-// out[0..n] = exclusive prefix sums of in[0..n), out[n] = total.
-cudaError_t launch_ti_scan(const uint32_t *in, int64_t n, int64_t *out, cudaStream_t st);
+// out[0..n] = exclusive prefix sums of in[0..n), out[n] = total; scratch holds
+// ti_scan_scratch(n) bytes.
+size_t ti_scan_scratch(int64_t n);
+cudaError_t launch_ti_scan(const uint32_t *in, int64_t n, int64_t *out, int64_t *scratch, cudaStream_t st);
 // m bounds of the listed centroids (list NULL: centroids 0..n-1).
 cudaError_t launch_ti_mtab(const uint32_t *hist, const int32_t *list, int32_t n, int32_t k, int L, const TiThr &thr,
                            uint8_t *mtab, cudaStream_t st);

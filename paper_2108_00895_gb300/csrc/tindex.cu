@@ -42,7 +42,6 @@
 namespace skm {
 
 constexpr int TI_WARPS = 8;
-constexpr uint32_t TI_KEY0 = 1536;   // float bits >> 19 of 2^-31, the lowest bin's lower edge
 
 constexpr int TI_STAGE = 64;   // most nonzeros of a document the query serves
 constexpr int TI_CAND = 256;   // most candidates it scores
@@ -58,11 +57,6 @@ __host__ __device__ __forceinline__ int ti_mbucket(uint32_t m) {
     int b = 0;
     while (b < TI_MB - 1 && (1u << b) < m) ++b;
     return b;
-}
-
-__device__ __forceinline__ int ti_bin(float v) {
-    const int key = (int)(__float_as_uint(fabsf(v)) >> 19) - (int)TI_KEY0;
-    return key < 0 ? 0 : (key > TI_NB - 1 ? TI_NB - 1 : key);
 }
 
 // Upper edge of bin b (every |value| in the bin is below it); the top bin is open.
@@ -103,42 +97,107 @@ __global__ void k_ti_rows(const float *C, int64_t ldc, int32_t d, int32_t k, int
     }
 }
 
+// Row counts from the bitmap alone (the update keeps G current): one warp per row.
+__global__ void k_ti_gcnt(const uint32_t *G, int32_t d, int32_t W, uint32_t *gcnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = warp; t < d; t += nwarps) {
+        uint32_t n = 0;
+        for (int w = lane; w < W; w += 32) n += __popc(__ldg(G + t * W + w));
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) n += __shfl_xor_sync(FULL, n, off);
+        if (lane == 0) gcnt[t] = n;
+    }
+}
+
+// Bin counts of the recomputed centroids restart from zero before the update's write pass
+// adds one per nonzero it stores. One block per moved centroid.
+__global__ void k_ti_zero_hist(const int32_t *moved, const int32_t *sizes, int32_t n_moved, uint32_t *hist) {
+    const int32_t j = moved[blockIdx.x];
+    if (sizes[j] <= 0) return;   // a cluster left empty keeps its centroid and its bins
+    for (int b = threadIdx.x; b < TI_NB; b += blockDim.x) hist[(size_t)j * TI_NB + b] = 0u;
+}
+
 // ------------------------------------------------------------------------------------
-// Exclusive prefix sums of n uint32 counts into int64 offsets (out[n] = total): one block,
-// tiles of 1024 x 4 elements in order (deterministic).
+// Exclusive prefix sums of n uint32 counts into int64 offsets (out[n] = total), in three
+// launches: chunk totals (TI_SCAN_CHUNK elements a block), one block scanning the totals,
+// and chunk-local scans from the chunk's offset. Integer sums: the same for any order.
 // ------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_ti_scan(const uint32_t *in, int64_t n, int64_t *out) {
-    __shared__ int64_t part[1024];
+constexpr int TI_SCAN_THREADS = 512;
+constexpr int TI_SCAN_PER = 8;
+constexpr int TI_SCAN_CHUNK = TI_SCAN_THREADS * TI_SCAN_PER;
+
+// Block-wide inclusive scan of one value a thread (warp shuffles, then the warp totals).
+__device__ __forceinline__ int64_t ti_block_scan(int64_t v, int64_t *wsum) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int64_t o = __shfl_up_sync(FULL, v, off);
+        if (lane >= off) v += o;
+    }
+    if (lane == 31) wsum[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t t = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int64_t o = __shfl_up_sync(FULL, t, off);
+            if (lane >= off) t += o;
+        }
+        if (lane < (int)(blockDim.x >> 5)) wsum[lane] = t;
+    }
+    __syncthreads();
+    const int64_t r = v + (wid > 0 ? wsum[wid - 1] : 0);
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(TI_SCAN_THREADS) k_ti_scan_sums(const uint32_t *in, int64_t n, int64_t *sums) {
+    __shared__ int64_t wsum[32];
+    const int64_t i0 = (int64_t)blockIdx.x * TI_SCAN_CHUNK + (int64_t)threadIdx.x * TI_SCAN_PER;
+    int64_t s = 0;
+#pragma unroll
+    for (int q = 0; q < TI_SCAN_PER; ++q)
+        if (i0 + q < n) s += in[i0 + q];
+    s = ti_block_scan(s, wsum);
+    if (threadIdx.x == blockDim.x - 1) sums[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(1024) k_ti_scan_top(int64_t *sums, int64_t nb, int64_t *total) {
+    __shared__ int64_t wsum[32];
     __shared__ int64_t carry;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
-    for (int64_t b0 = 0; b0 < n; b0 += 4096) {
-        const int64_t i0 = b0 + (int64_t)threadIdx.x * 4;
-        int64_t v[4], s = 0;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            v[q] = i0 + q < n ? (int64_t)in[i0 + q] : 0;
-            s += v[q];
-        }
-        part[threadIdx.x] = s;
+    for (int64_t b0 = 0; b0 < nb; b0 += blockDim.x) {
+        const int64_t b = b0 + threadIdx.x;
+        const int64_t v = b < nb ? sums[b] : 0;
+        const int64_t inc = ti_block_scan(v, wsum);
+        const int64_t c = carry;
+        if (b < nb) sums[b] = c + inc - v;   // exclusive offset of chunk b
         __syncthreads();
-        for (int off = 1; off < 1024; off <<= 1) {
-            const int64_t o = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0;
-            __syncthreads();
-            part[threadIdx.x] += o;
-            __syncthreads();
-        }
-        int64_t run = carry + part[threadIdx.x] - s;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (i0 + q < n) out[i0 + q] = run;
-            run += v[q];
-        }
-        __syncthreads();
-        if (threadIdx.x == 1023) carry += part[1023];
+        if (threadIdx.x == blockDim.x - 1) carry = c + inc;
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[n] = carry;
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void __launch_bounds__(TI_SCAN_THREADS) k_ti_scan_out(const uint32_t *in, int64_t n, const int64_t *sums,
+                                                                 int64_t *out) {
+    __shared__ int64_t wsum[32];
+    const int64_t i0 = (int64_t)blockIdx.x * TI_SCAN_CHUNK + (int64_t)threadIdx.x * TI_SCAN_PER;
+    int64_t v[TI_SCAN_PER], s = 0;
+#pragma unroll
+    for (int q = 0; q < TI_SCAN_PER; ++q) {
+        v[q] = i0 + q < n ? (int64_t)in[i0 + q] : 0;
+        s += v[q];
+    }
+    int64_t run = sums[blockIdx.x] + ti_block_scan(s, wsum) - s;
+#pragma unroll
+    for (int q = 0; q < TI_SCAN_PER; ++q) {
+        if (i0 + q < n) out[i0 + q] = run;
+        run += v[q];
+    }
 }
 
 // ------------------------------------------------------------------------------------
@@ -221,22 +280,29 @@ __global__ void __launch_bounds__(TI_FILL_WARPS * 32) k_ti_fill(const float *C, 
         if (lane < TI_MAXL * TI_MB) at[lane] = 0u;
         __syncwarp();
         for (int pass = 0; pass < 2; ++pass) {
-            for (int w = 0; w < W; ++w) {
-                const uint32_t g = __ldg(G + t * W + w);
-                if (g == 0u) continue;
-                const int j = w * 32 + lane;
-                const bool nz = (g >> lane) & 1u;
-                const int bin = nz ? ti_bin(__ldg(row + j)) : 0;
-                for (int l = 0; l < L; ++l) {
-                    const uint32_t m = nz ? (uint32_t)__ldg(mtab + ((size_t)l * k + j) * TI_NB + bin) : 0u;
-                    const int key = m ? ti_mbucket(m) : -1;
-                    const unsigned grp = __match_any_sync(FULL, key);
-                    const bool lead = key >= 0 && lane == __ffs(grp) - 1;
-                    if (pass == 1 && key >= 0)
-                        P[(int64_t)l * nzC + base + at[l * TI_MB + key] + __popc(grp & below)] = ((uint32_t)j << 8) | m;
-                    __syncwarp();
-                    if (lead) at[l * TI_MB + key] += __popc(grp);
-                    __syncwarp();
+            // the row's bitmap words 32 at a time; the warp visits the nonzero ones
+            for (int w0 = 0; w0 < W; w0 += 32) {
+                const uint32_t gl = w0 + lane < W ? __ldg(G + t * W + w0 + lane) : 0u;
+                unsigned todo = __ballot_sync(FULL, gl != 0u);
+                while (todo) {
+                    const int qw = __ffs(todo) - 1;
+                    todo &= todo - 1u;
+                    const uint32_t g = __shfl_sync(FULL, gl, qw);
+                    const int j = (w0 + qw) * 32 + lane;
+                    const bool nz = (g >> lane) & 1u;
+                    const int bin = nz ? ti_bin(__ldg(row + j)) : 0;
+                    for (int l = 0; l < L; ++l) {
+                        const uint32_t m = nz ? (uint32_t)__ldg(mtab + ((size_t)l * k + j) * TI_NB + bin) : 0u;
+                        const int key = m ? ti_mbucket(m) : -1;
+                        const unsigned grp = __match_any_sync(FULL, key);
+                        const bool lead = key >= 0 && lane == __ffs(grp) - 1;
+                        if (pass == 1 && key >= 0)
+                            P[(int64_t)l * nzC + base + at[l * TI_MB + key] + __popc(grp & below)] =
+                                ((uint32_t)j << 8) | m;
+                        __syncwarp();
+                        if (lead) at[l * TI_MB + key] += __popc(grp);
+                        __syncwarp();
+                    }
                 }
             }
             if (pass == 0) {
@@ -263,13 +329,40 @@ __global__ void __launch_bounds__(TI_FILL_WARPS * 32) k_ti_fill(const float *C, 
 // few memory round trips per document rather than one per term.
 // Shared memory per warp (32-bit words): the staged terms, values and baseline entries,
 // the list offsets (64-bit), lengths and prefix sums; the 8 count planes of each bitmap
-// word (word w's at [8w, 8w + 8), read as two 16-byte vectors), the candidate bits and
-// the candidate list; rounded up to 16 bytes.
+// word (word w's at [8w, 8w + 8), read and written as two 16-byte vectors), the candidate
+// bits and the candidate list; rounded up to 16 bytes.
 // A document goes to the dense passes when no threshold is below its baseline, when it
 // has more than TI_STAGE nonzeros, or when its candidates would cost more to score one
 // by one (a 32-byte sector per product) than a dense pass over all k (elt bytes per
 // product): more than min(TI_CAND, k elt / 32) candidates (or the configured cap).
 // ------------------------------------------------------------------------------------
+// Carry-save adder: a + b + c = 2 h + l in every bit position.
+__device__ __forceinline__ void ti_csa(uint32_t &h, uint32_t &l, uint32_t a, uint32_t b, uint32_t c) {
+    const uint32_t u = a ^ b;
+    h = (a & b) | (u & c);
+    l = u ^ c;
+}
+
+// Adds 8 bit vectors to the bit-sliced counters c (plane q holds bit q of each position's
+// count; the counts stay below 256): a tree of carry-save adders into the planes of weight
+// 1, 2 and 4, whose weight-8 carries are then added to planes 3.. with ripple carries.
+__device__ __forceinline__ void ti_add8(uint32_t (&c)[TI_PLANES], const uint32_t (&g)[8]) {
+    uint32_t tA, tB, fA, fB, e;
+    ti_csa(tA, c[0], c[0], g[0], g[1]);
+    ti_csa(tB, c[0], c[0], g[2], g[3]);
+    ti_csa(fA, c[1], c[1], tA, tB);
+    ti_csa(tA, c[0], c[0], g[4], g[5]);
+    ti_csa(tB, c[0], c[0], g[6], g[7]);
+    ti_csa(fB, c[1], c[1], tA, tB);
+    ti_csa(e, c[2], c[2], fA, fB);
+#pragma unroll
+    for (int q = 3; q < TI_PLANES; ++q) {
+        const uint32_t nq = c[q] ^ e;
+        e &= c[q];
+        c[q] = nq;
+    }
+}
+
 struct TiWarpSmem {
     int32_t *t;
     float *x;
@@ -390,15 +483,16 @@ __global__ void __launch_bounds__(TI_WARPS * 32) k_ti_query(TiQueryArgs a) {
             sm.off[p] = __ldg(a.gptr + t);
             sm.len[p] = __ldg(pbe + (int64_t)t * TI_MB);
         }
-        // overlap counts: bit-sliced 8-bit counters (ripple-carry adds; nnz <= 64 < 256),
-        // lane-owned words in groups of 4, kept in shared memory between term batches of 8;
-        // a group's 32 bitmap words are loaded before any is added
+        // overlap counts: bit-sliced 8-bit counters (nnz <= 64 < 256), lane-owned words in
+        // groups of 4, kept in shared memory between term batches of 8; a group's 32 bitmap
+        // words are loaded before any is added, 8 at a time by a carry-save adder tree
         for (int w0 = lane; w0 < W; w0 += 32 * 4) {
             for (int u = 0; u < 4; ++u) {
                 const int w = w0 + 32 * u;
                 if (w < W) {
-#pragma unroll
-                    for (int q = 0; q < TI_PLANES; ++q) sm.pl[TI_PLANES * w + q] = 0u;
+                    uint4 *v = reinterpret_cast<uint4 *>(sm.pl + TI_PLANES * w);
+                    v[0] = make_uint4(0u, 0u, 0u, 0u);
+                    v[1] = make_uint4(0u, 0u, 0u, 0u);
                     sm.cb[w] = 0u;
                 }
             }
@@ -416,20 +510,13 @@ __global__ void __launch_bounds__(TI_WARPS * 32) k_ti_query(TiQueryArgs a) {
                     const int w = w0 + 32 * u;
                     if (w >= W) break;
                     uint32_t c[TI_PLANES];
-#pragma unroll
-                    for (int q = 0; q < TI_PLANES; ++q) c[q] = sm.pl[TI_PLANES * w + q];
-#pragma unroll
-                    for (int v = 0; v < 8; ++v) {
-                        uint32_t cy = g[u][v];
-#pragma unroll
-                        for (int q = 0; q < TI_PLANES; ++q) {
-                            const uint32_t nq = c[q] ^ cy;
-                            cy &= c[q];
-                            c[q] = nq;
-                        }
-                    }
-#pragma unroll
-                    for (int q = 0; q < TI_PLANES; ++q) sm.pl[TI_PLANES * w + q] = c[q];
+                    uint4 *v = reinterpret_cast<uint4 *>(sm.pl + TI_PLANES * w);
+                    const uint4 lo = v[0], hi = v[1];
+                    c[0] = lo.x; c[1] = lo.y; c[2] = lo.z; c[3] = lo.w;
+                    c[4] = hi.x; c[5] = hi.y; c[6] = hi.z; c[7] = hi.w;
+                    ti_add8(c, g[u]);
+                    v[0] = make_uint4(c[0], c[1], c[2], c[3]);
+                    v[1] = make_uint4(c[4], c[5], c[6], c[7]);
                 }
             }
         }
@@ -587,8 +674,29 @@ cudaError_t launch_ti_rows(const float *C, int64_t ldc, int32_t d, int32_t k, ui
     return cudaGetLastError();
 }
 
-cudaError_t launch_ti_scan(const uint32_t *in, int64_t n, int64_t *out, cudaStream_t st) {
-    k_ti_scan<<<1, 1024, 0, st>>>(in, n, out);
+cudaError_t launch_ti_gcnt(const uint32_t *G, int32_t d, int32_t W, uint32_t *gcnt, cudaStream_t st) {
+    k_ti_gcnt<<<row_blocks(d), 256, 0, st>>>(G, d, W, gcnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ti_zero_hist(const int32_t *moved, const int32_t *sizes, int32_t n_moved, uint32_t *hist,
+                                cudaStream_t st) {
+    if (n_moved <= 0) return cudaSuccess;
+    k_ti_zero_hist<<<n_moved, 128, 0, st>>>(moved, sizes, n_moved, hist);
+    return cudaGetLastError();
+}
+
+size_t ti_scan_scratch(int64_t n) { return sizeof(int64_t) * (size_t)((n + TI_SCAN_CHUNK - 1) / TI_SCAN_CHUNK + 1); }
+
+cudaError_t launch_ti_scan(const uint32_t *in, int64_t n, int64_t *out, int64_t *scratch, cudaStream_t st) {
+    const int64_t nb = (n + TI_SCAN_CHUNK - 1) / TI_SCAN_CHUNK;
+    if (nb > 0) {
+        k_ti_scan_sums<<<(unsigned)nb, TI_SCAN_THREADS, 0, st>>>(in, n, scratch);
+        k_ti_scan_top<<<1, 1024, 0, st>>>(scratch, nb, out + n);
+        k_ti_scan_out<<<(unsigned)nb, TI_SCAN_THREADS, 0, st>>>(in, n, scratch, out);
+    } else {
+        k_ti_scan_top<<<1, 1024, 0, st>>>(scratch, 0, out + n);
+    }
     return cudaGetLastError();
 }
 

@@ -331,6 +331,10 @@ __device__ __forceinline__ void update_entry(const UpdateArgs &u, int32_t t, int
         else
             reinterpret_cast<float *>(u.CM)[row + m] = c;
     }
+    if (u.tiG && c != 0.f) {   // keep the threshold index's bitmap and value bins current
+        atomicOr(u.tiG + (int64_t)t * u.tiW + (j >> 5), 1u << (j & 31));
+        atomicAdd(u.tiHist + (size_t)j * TI_NB + ti_bin(c), 1u);
+    }
     const double c2 = (double)c * (double)c;   // exact (24-bit mantissa squared)
     const unsigned long long q = (unsigned long long)__double2ull_rn(ldexp(c2, 62));
     atomic_add_u128(dst, q, 0ull);
@@ -524,19 +528,28 @@ cudaError_t launch_from_u128(const unsigned long long *normsq128, const unsigned
 //   k_zero_seeds: a centroid that is still its seed document: that document's terms;
 //   k_zero_cols: any other column (a centroid kept while its cluster was empty): all rows.
 // ------------------------------------------------------------------------------------
+// Clears bit (t, j) of the threshold-index bitmap (W words a row).
+__device__ __forceinline__ void ti_clear_bit(uint32_t *G, int32_t W, int64_t t, int32_t j) {
+    atomicAnd(G + t * W + (j >> 5), ~(1u << (j & 31)));
+}
+
 __global__ void k_zero_members(const int32_t *row_idx, const int32_t *pterm, int64_t nnz, const int32_t *a_old,
-                               const uint8_t *flag, float *C32, __nv_bfloat16 *C16, int64_t ldc) {
+                               const uint8_t *flag, float *C32, __nv_bfloat16 *C16, int64_t ldc, uint32_t *tiG,
+                               int32_t W) {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
         const int32_t j = __ldg(a_old + __ldg(row_idx + p));
         if (!__ldg(flag + j)) continue;
-        const int64_t e = (int64_t)__ldg(pterm + p) * ldc + j;
+        const int64_t t = (int64_t)__ldg(pterm + p);
+        const int64_t e = t * ldc + j;
         C32[e] = 0.f;
         if (C16) C16[e] = __float2bfloat16_rn(0.f);
+        if (tiG) ti_clear_bit(tiG, W, t, j);
     }
 }
 
 __global__ void k_zero_seeds(const int32_t *list, int32_t n, const int32_t *init_ids, const int64_t *row_ptr,
-                             const int32_t *col, float *C32, __nv_bfloat16 *C16, int64_t ldc) {
+                             const int32_t *col, float *C32, __nv_bfloat16 *C16, int64_t ldc, uint32_t *tiG,
+                             int32_t W) {
     const int lane = threadIdx.x & 31;
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (w >= n) return;
@@ -546,16 +559,19 @@ __global__ void k_zero_seeds(const int32_t *list, int32_t n, const int32_t *init
         const int64_t e = (int64_t)col[p] * ldc + j;
         C32[e] = 0.f;
         if (C16) C16[e] = __float2bfloat16_rn(0.f);
+        if (tiG) ti_clear_bit(tiG, W, col[p], j);
     }
 }
 
-__global__ void k_zero_cols(const int32_t *list, int32_t n, int32_t d, float *C32, __nv_bfloat16 *C16, int64_t ldc) {
+__global__ void k_zero_cols(const int32_t *list, int32_t n, int32_t d, float *C32, __nv_bfloat16 *C16, int64_t ldc,
+                            uint32_t *tiG, int32_t W) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
     const int32_t j = list[q];
     for (int64_t t = blockIdx.y; t < d; t += gridDim.y) {
         C32[t * ldc + j] = 0.f;
         if (C16) C16[t * ldc + j] = __float2bfloat16_rn(0.f);
+        if (tiG) ti_clear_bit(tiG, W, t, j);
     }
 }
 
@@ -583,25 +599,27 @@ static unsigned rows_grid(int32_t d, unsigned bx) {
 }
 
 cudaError_t launch_zero_members(const int32_t *row_idx, const int32_t *pterm, int64_t nnz, const int32_t *a_old,
-                                const uint8_t *flag, float *C32, __nv_bfloat16 *C16, int64_t ldc, cudaStream_t st) {
+                                const uint8_t *flag, float *C32, __nv_bfloat16 *C16, int64_t ldc, uint32_t *tiG,
+                                int32_t W, cudaStream_t st) {
     if (nnz <= 0) return cudaSuccess;
     const int64_t blocks = std::min<int64_t>((nnz + 255) / 256, 152 * 16);
-    k_zero_members<<<(unsigned)blocks, 256, 0, st>>>(row_idx, pterm, nnz, a_old, flag, C32, C16, ldc);
+    k_zero_members<<<(unsigned)blocks, 256, 0, st>>>(row_idx, pterm, nnz, a_old, flag, C32, C16, ldc, tiG, W);
     return cudaGetLastError();
 }
 
 cudaError_t launch_zero_seeds(const int32_t *list, int32_t n, const int32_t *init_ids, const int64_t *row_ptr,
-                              const int32_t *col, float *C32, __nv_bfloat16 *C16, int64_t ldc, cudaStream_t st) {
+                              const int32_t *col, float *C32, __nv_bfloat16 *C16, int64_t ldc, uint32_t *tiG,
+                              int32_t W, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    k_zero_seeds<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(list, n, init_ids, row_ptr, col, C32, C16, ldc);
+    k_zero_seeds<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(list, n, init_ids, row_ptr, col, C32, C16, ldc, tiG, W);
     return cudaGetLastError();
 }
 
 cudaError_t launch_zero_cols(const int32_t *list, int32_t n, int32_t d, float *C32, __nv_bfloat16 *C16, int64_t ldc,
-                             cudaStream_t st) {
+                             uint32_t *tiG, int32_t W, cudaStream_t st) {
     if (n <= 0 || d <= 0) return cudaSuccess;
     const unsigned bx = (unsigned)((n + 255) / 256);
-    k_zero_cols<<<dim3(bx, rows_grid(d, bx)), 256, 0, st>>>(list, n, d, C32, C16, ldc);
+    k_zero_cols<<<dim3(bx, rows_grid(d, bx)), 256, 0, st>>>(list, n, d, C32, C16, ldc, tiG, W);
     return cudaGetLastError();
 }
 

@@ -159,3 +159,23 @@ def test_invalid_index_arguments(skm):
     for bad in ([0.5, 0.25], [0.0], [1.5], [0.1] * 5):
         with pytest.raises((skm.SkmError, ValueError)):
             skm.SphericalKMeans(8, prune="ncc_index", index_lambdas=bad)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_index_kept_by_the_update_equals_a_fresh_build(skm, precision):
+    """After a fit with the index, the bitmap and value bins that the update kept current give
+    the same candidate sets as an index built from scratch on the final centroids."""
+    w = SHAPES["tweets"]
+    docs = w.corpus()
+    ids = w.init_ids()
+    with skm.SphericalKMeans(w.k, precision=precision, prune="ncc_index", max_iter=8, index_min_changed=-1,
+                             index_max_cands=512) as km:
+        r = km.fit(docs, ids)
+        assert r.stats["index_docs"] > 0
+        C = km.centroids()
+        kept = [km.index_candidates(docs, level) for level in range(len(LAMBDAS))]
+    with skm.SphericalKMeans(w.k, precision=precision, prune="ncc_index") as km:
+        km.set_centroids(C)
+        fresh = [km.index_candidates(docs, level) for level in range(len(LAMBDAS))]
+    for level in range(len(LAMBDAS)):
+        np.testing.assert_array_equal(kept[level], fresh[level])
