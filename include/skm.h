@@ -100,10 +100,12 @@ typedef struct {
     int32_t index_min_changed; /* the index serves a step only when more than this many
                                   centroids changed in the previous update (Sec. 4.3
                                   suggests 100, the default); -1: every step after the first */
-    int32_t index_max_cands; /* a document with more candidates than this is scored densely:
-                                0 (the default) = min(512, k * (element bytes) / 32), where
+    int32_t index_max_cands; /* a document with more candidates than this is scored densely.
+                                0 (the default): min(256, k * (element bytes) / 32), where
                                 scoring the candidates one by one (a 32-byte sector per
-                                product) stops being cheaper than a dense pass; at most 512 */
+                                product) stops being cheaper than a dense pass, and documents
+                                whose list walk exceeds nnz * k / 16 entries are scored
+                                densely too. > 0: that cap (at most 256), no walk rule. */
 } skm_config;
 
 /* Fills a config with defaults: FP32, no pruning, max_iter 20, shift test off, rescoring

@@ -74,11 +74,12 @@ def test_candidates_contain_oracle_candidates_and_every_high_similarity(skm, sha
             assert short.sum() > 0.3 * docs.n_docs
 
 
-@pytest.mark.parametrize("precision,cap", [("fp32", 512), ("bf16", 512), ("fp32", 0)])
+@pytest.mark.parametrize("precision,cap", [("fp32", 256), ("bf16", 256), ("fp32", 0)])
 @pytest.mark.parametrize("shape", list(SHAPES))
 def test_fit_with_index_equals_full_fit_bit_for_bit(skm, shape, precision, cap):
-    """cap 512 indexes every short document whose baseline reaches a threshold; cap 0 (the
-    automatic cost rule) sends those with many candidates to the dense passes."""
+    """cap 256 indexes every short document whose baseline reaches a threshold (up to 256
+    candidates); cap 0 (the automatic cost rules) sends those with long walks or many
+    candidates to the dense passes."""
     w = SHAPES[shape]
     docs = w.corpus()
     ids = w.init_ids()
@@ -105,7 +106,7 @@ def test_fit_with_index_matches_oracle_ncc_index(skm, shape):
     ids = w.init_ids()
     ref = oracle.fit(docs, w.k, ids, w.max_iter, mode="ncc_index", index_min_changed=-1)
     with skm.SphericalKMeans(w.k, prune="ncc_index", max_iter=w.max_iter, index_min_changed=-1,
-                             index_max_cands=512) as km:
+                             index_max_cands=256) as km:
         r = km.fit(docs, ids)
         C = km.centroids()
     assert r.iters == ref.iters
@@ -123,7 +124,7 @@ def test_index_min_changed_gates_the_index(skm):
     out = {}
     for gate in (-1, 40, 10 ** 9):
         with skm.SphericalKMeans(w.k, prune="ncc_index", max_iter=w.max_iter, index_min_changed=gate,
-                                 index_max_cands=512) as km:
+                                 index_max_cands=256) as km:
             out[gate] = km.fit(docs, ids)
     assert out[10 ** 9].stats["index_docs"] == 0
     assert out[-1].stats["index_docs"] > out[40].stats["index_docs"] > 0
@@ -141,7 +142,7 @@ def test_custom_thresholds_and_documents_below_every_threshold(skm):
     with skm.SphericalKMeans(w.k, prune="none", max_iter=w.max_iter) as km:
         full = km.fit(docs, ids)
     with skm.SphericalKMeans(w.k, prune="ncc_index", max_iter=w.max_iter, index_min_changed=-1,
-                             index_lambdas=[0.95], index_max_cands=512) as km:
+                             index_lambdas=[0.95], index_max_cands=256) as km:
         r = km.fit(docs, ids)
     np.testing.assert_array_equal(r.assign, full.assign)
     np.testing.assert_array_equal(r.objective, full.objective)
@@ -169,7 +170,7 @@ def test_index_kept_by_the_update_equals_a_fresh_build(skm, precision):
     docs = w.corpus()
     ids = w.init_ids()
     with skm.SphericalKMeans(w.k, precision=precision, prune="ncc_index", max_iter=8, index_min_changed=-1,
-                             index_max_cands=512) as km:
+                             index_max_cands=256) as km:
         r = km.fit(docs, ids)
         assert r.stats["index_docs"] > 0
         C = km.centroids()
