@@ -101,11 +101,14 @@ typedef struct {
                                   centroids changed in the previous update (Sec. 4.3
                                   suggests 100, the default); -1: every step after the first */
     int32_t index_max_cands; /* a document with more candidates than this is scored densely.
-                                0 (the default): min(256, k * (element bytes) / 32), where
-                                scoring the candidates one by one (a 32-byte sector per
-                                product) stops being cheaper than a dense pass, and documents
-                                whose list walk exceeds nnz * k / 16 entries are scored
-                                densely too. > 0: that cap (at most 256), no walk rule. */
+                                0 (the default) selects the automatic cost rules: the cap is
+                                min(256, k * (element bytes) / 32), where scoring candidates
+                                one by one (a 32-byte sector per product) stops being cheaper
+                                than a dense pass; documents whose list walk exceeds
+                                nnz * k / 16 entries are scored densely; the index serves only
+                                k >= 1024, and stops for the rest of a fit after a step that
+                                decided fewer than half of the documents through it.
+                                > 0: that cap (at most 256) and none of those rules. */
 } skm_config;
 
 /* Fills a config with defaults: FP32, no pruning, max_iter 20, shift test off, rescoring

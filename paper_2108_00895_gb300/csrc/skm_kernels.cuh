@@ -200,6 +200,7 @@ constexpr int TI_MAXL = 4;     // thresholds (lambda levels)
 constexpr int TI_MB = 8;       // m buckets of each term's list
 constexpr int TI_PLANES = 8;   // bits of the overlap counts and of the stored m bounds
 constexpr int32_t TI_MAX_K = 16384;
+constexpr int32_t TI_AUTO_MIN_K = 1024;   // automatic mode: smallest k the index serves
 __host__ __device__ constexpr int32_t ti_words(int32_t k) { return (k + 31) / 32; }
 
 constexpr uint32_t TI_KEY0 = 1536;   // float bits >> 19 of 2^-31, the lowest bin's lower edge
