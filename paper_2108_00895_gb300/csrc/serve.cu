@@ -27,6 +27,7 @@
 
 #include "skm.h"
 #include "skm_host.h"
+#include "skm_internal.cuh"
 
 namespace {
 
@@ -77,7 +78,7 @@ namespace {
 // Device memory a clustering job may hold (mirrors the context's allocations, rounded up).
 size_t fit_estimate(const skm_csr &d, int32_t k, int precision, int prune) {
     const size_t n = (size_t)d.n_docs, e = (size_t)d.nnz, t = (size_t)d.n_terms;
-    const int slice = precision == SKM_BF16 ? (k <= 256 ? 256 : 512) : (k <= 128 ? 128 : 256);
+    const int slice = skm::slice_width(precision, k, (double)e / (double)(n > 0 ? n : 1));
     const size_t ldc = ((size_t)k + slice - 1) / slice * slice;
     const size_t cent = t * ldc * (precision == SKM_BF16 ? (4 + 2 + 2) : (4 + 4));
     const size_t docs = (n + 1) * 8 + e * 8;

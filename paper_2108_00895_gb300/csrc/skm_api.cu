@@ -1178,6 +1178,9 @@ skm_status skm_fit(skm_ctx *ctx, const skm_csr *docs, const int32_t *init_doc_id
     DevCsr dc{};
     SKM_TRY(stage_docs(ctx, docs, dc));
     const int64_t N = dc.n;
+    // the fit lays the centroid matrices out anew: the slice width follows the documents
+    ctx->slice = slice_width(ctx->cfg.precision, k, (double)dc.nnz / (double)N);
+    ctx->ldc = ((int64_t)k + ctx->slice - 1) / ctx->slice * ctx->slice;
     SKM_TRY(ensure_centroids(ctx, dc.d, true, true));
     SKM_TRY(ensure_cluster_bufs(ctx));
     SKM_TRY(ensure_doc_bufs(ctx, N));

@@ -125,7 +125,8 @@ cudaError_t launch_score(const ScoreArgs &a, int precision, int slice_cols, cuda
                          const SparseArgs *sp = nullptr);
 cudaError_t launch_collect(const ScoreArgs &a, int precision, int slice_cols, cudaStream_t st,
                            const SparseArgs *sp = nullptr);
-int slice_width(int precision, int k);   // KS for the scoring kernel
+// KS for the scoring kernel, given the mean nonzeros of the documents it will score
+int slice_width(int precision, int k, double mean_nnz = 1e9);
 
 // Sparse-row index (defined in rare.cu). M is a term-major d x ldc matrix (FP32 for
 // precision 0, BF16 for 1) whose first ncols columns are valid.
