@@ -57,6 +57,7 @@ struct skm_ctx {
     Buf d_row_ptr, d_col, d_val;
     // transposed postings
     Buf col_ptr, row_idx, cval, pterm, tcount, light_t0, light_t1, heavy_terms;
+    Buf vh_terms, vch_h, vch_p0, vch_p1, vh_sum;   // very frequent terms, split into chunks
     // per-document state
     Buf abuf[2], s_state, r_state, clean, mdoc, order, order_hist;
     Buf part_s, part_j;
@@ -391,6 +392,8 @@ skm_status ensure_doc_bufs(skm_ctx *ctx, int64_t n) {
 struct Postings {
     int32_t n_light = 0;   // chunks of consecutive light terms
     int32_t n_heavy = 0;   // terms with more postings than a chunk holds
+    int32_t n_vh = 0;      // of those, the very frequent terms summed in chunks
+    int32_t n_vch = 0;     // their chunks
     int F = 0;             // fixed-point bits of the update sums
     int64_t d_eff = 0;     // terms with at least one posting
 };
@@ -436,10 +439,32 @@ skm_status build_postings(skm_ctx *ctx, const DevCsr &dc, Postings &pg) {
         start = -1;
         w = 0;
     };
+    // very frequent terms go to the split path, most frequent first, as long as their sums
+    // (one 64-bit integer per moved cluster) fit in 512 MB
+    std::vector<int32_t> by_count;
+    for (int32_t t = 0; t < d; ++t)
+        if (cnt[t] > update_vh_postings()) by_count.push_back(t);
+    std::sort(by_count.begin(), by_count.end(), [&](int32_t x, int32_t y) { return cnt[x] > cnt[y] || (cnt[x] == cnt[y] && x < y); });
+    const size_t vh_cap = (size_t(512) << 20) / (sizeof(unsigned long long) * (size_t)std::max(k, 1));
+    if (by_count.size() > vh_cap) by_count.resize(vh_cap);
+    std::vector<uint8_t> is_vh(d, 0);
+    for (int32_t t : by_count) is_vh[t] = 1;
+    std::vector<int32_t> vh, vch_h;
+    std::vector<int64_t> vch_p0, vch_p1;
     for (int32_t t = 0; t < d; ++t) {
         if (cnt[t] > chunk) {          // a chunk's posting range never spans a heavy term
             close(t);
-            heavy.push_back(t);
+            if (is_vh[t]) {
+                const int32_t h = (int32_t)vh.size();
+                vh.push_back(t);
+                for (int64_t p = cp[t]; p < cp[t + 1]; p += update_vh_chunk()) {
+                    vch_h.push_back(h);
+                    vch_p0.push_back(p);
+                    vch_p1.push_back(std::min<int64_t>(p + update_vh_chunk(), cp[t + 1]));
+                }
+            } else {
+                heavy.push_back(t);
+            }
             continue;
         }
         if (cnt[t] == 0) continue;
@@ -451,6 +476,19 @@ skm_status build_postings(skm_ctx *ctx, const DevCsr &dc, Postings &pg) {
     if (start >= 0) close(last + 1);
     pg.n_light = (int32_t)l0.size();
     pg.n_heavy = (int32_t)heavy.size();
+    pg.n_vh = (int32_t)vh.size();
+    pg.n_vch = (int32_t)vch_h.size();
+    if (pg.n_vh) {
+        SKM_TRY(ensure(ctx, ctx->vh_terms, sizeof(int32_t) * pg.n_vh));
+        SKM_TRY(ensure(ctx, ctx->vch_h, sizeof(int32_t) * pg.n_vch));
+        SKM_TRY(ensure(ctx, ctx->vch_p0, sizeof(int64_t) * pg.n_vch));
+        SKM_TRY(ensure(ctx, ctx->vch_p1, sizeof(int64_t) * pg.n_vch));
+        SKM_TRY(ensure(ctx, ctx->vh_sum, sizeof(unsigned long long) * (size_t)pg.n_vh * k));
+        SKM_CUDA(cudaMemcpyAsync(ctx->vh_terms.p, vh.data(), sizeof(int32_t) * pg.n_vh, cudaMemcpyHostToDevice, ctx->st));
+        SKM_CUDA(cudaMemcpyAsync(ctx->vch_h.p, vch_h.data(), sizeof(int32_t) * pg.n_vch, cudaMemcpyHostToDevice, ctx->st));
+        SKM_CUDA(cudaMemcpyAsync(ctx->vch_p0.p, vch_p0.data(), sizeof(int64_t) * pg.n_vch, cudaMemcpyHostToDevice, ctx->st));
+        SKM_CUDA(cudaMemcpyAsync(ctx->vch_p1.p, vch_p1.data(), sizeof(int64_t) * pg.n_vch, cudaMemcpyHostToDevice, ctx->st));
+    }
     SKM_TRY(ensure(ctx, ctx->light_t0, sizeof(int32_t) * std::max(pg.n_light, 1)));
     SKM_TRY(ensure(ctx, ctx->light_t1, sizeof(int32_t) * std::max(pg.n_light, 1)));
     SKM_TRY(ensure(ctx, ctx->heavy_terms, sizeof(int32_t) * std::max(pg.n_heavy, 1)));
@@ -907,6 +945,13 @@ skm_status update_step(skm_ctx *ctx, const DevCsr &dc, const Postings &pg, const
         u.light_t1 = P<int32_t>(ctx->light_t1);
         u.n_heavy = pg.n_heavy;
         u.heavy_terms = P<int32_t>(ctx->heavy_terms);
+        u.n_vh = pg.n_vh;
+        u.vh_terms = P<int32_t>(ctx->vh_terms);
+        u.vh_sum = P<unsigned long long>(ctx->vh_sum);
+        u.n_vch = pg.n_vch;
+        u.vch_h = P<int32_t>(ctx->vch_h);
+        u.vch_p0 = P<int64_t>(ctx->vch_p0);
+        u.vch_p1 = P<int64_t>(ctx->vch_p1);
         u.col_ptr = P<int64_t>(ctx->col_ptr);
         u.row_idx = P<int32_t>(ctx->row_idx);
         u.cval = P<float>(ctx->cval);
@@ -938,6 +983,7 @@ skm_status update_step(skm_ctx *ctx, const DevCsr &dc, const Postings &pg, const
         }
         SKM_CUDA(cudaMemsetAsync(u.normsq128, 0, 2 * sizeof(unsigned long long) * n_moved, ctx->st));
         SKM_CUDA(cudaMemsetAsync(u.sq128, 0, 2 * sizeof(unsigned long long) * n_moved, ctx->st));
+        SKM_CUDA(launch_update_vh_sums(u, ctx->st));
         SKM_CUDA(launch_update_norm(u, ctx->st));
         SKM_CUDA(launch_from_u128(u.normsq128, nullptr, n_moved, pg.F, P<double>(ctx->normsq), P<double>(ctx->inv_norm),
                                   nullptr, ctx->st));
@@ -1039,7 +1085,8 @@ skm_status skm_destroy(skm_ctx *ctx) {
     cudaStreamSynchronize(ctx->st);
     Buf *all[] = {&ctx->C32, &ctx->C16, &ctx->CM, &ctx->norm_store, &ctx->d_row_ptr, &ctx->d_col,
                   &ctx->d_val, &ctx->col_ptr, &ctx->row_idx, &ctx->cval, &ctx->pterm, &ctx->tcount,
-                  &ctx->light_t0, &ctx->light_t1, &ctx->heavy_terms, &ctx->abuf[0], &ctx->abuf[1], &ctx->s_state, &ctx->r_state,
+                  &ctx->light_t0, &ctx->light_t1, &ctx->heavy_terms, &ctx->vh_terms, &ctx->vch_h,
+                  &ctx->vch_p0, &ctx->vch_p1, &ctx->vh_sum, &ctx->abuf[0], &ctx->abuf[1], &ctx->s_state, &ctx->r_state,
                   &ctx->clean, &ctx->mdoc, &ctx->order, &ctx->order_hist, &ctx->part_s, &ctx->part_j, &ctx->list_a, &ctx->list_b, &ctx->rs_doc,
                   &ctx->rs_cand, &ctx->refull, &ctx->full64, &ctx->collect_doc, &ctx->collect_thr, &ctx->cand,
                   &ctx->cand_cnt, &ctx->changed, &ctx->sizes, &ctx->moved,

@@ -153,15 +153,29 @@ struct UpdateArgs {
     float *C32;
     __nv_bfloat16 *C16;        // nullable (FP32 mode)
     void *CM;                  // nullable: compacted moved matrix (precision of the scored copy)
+    // very frequent terms: their postings are split into chunks summed by many blocks into
+    // vh_sum[h * n_moved + m] (S of term vh_terms[h], moved position m), which the norm and
+    // write passes then read (update_vh_sums before the norm pass)
+    int32_t n_vh;
+    const int32_t *vh_terms;
+    unsigned long long *vh_sum;
+    int32_t n_vch;              // chunks: term index vch_h[c], postings [vch_p0[c], vch_p1[c])
+    const int32_t *vch_h;
+    const int64_t *vch_p0;
+    const int64_t *vch_p1;
     uint32_t *tiG;             // nullable: threshold-index bitmap to keep current (bits set
     uint32_t *tiHist;          //   for written nonzeros) and bin counts (one per nonzero)
     int32_t tiW;
     int precision;
     int64_t ldc;
 };
+// Sums of the very frequent terms (vh_sum zeroed here), before launch_update_norm.
+cudaError_t launch_update_vh_sums(const UpdateArgs &u, cudaStream_t st);
 cudaError_t launch_update_norm(const UpdateArgs &u, cudaStream_t st);
 cudaError_t launch_update_write(const UpdateArgs &u, cudaStream_t st);
 int update_chunk_postings();   // most postings of a light chunk
+int update_vh_postings();      // terms with more postings than this are split into chunks
+int update_vh_chunk();         // postings of one chunk of a split term
 // normsq, inv_norm (nullable source normsq128) and newsq (nullable source sq128).
 cudaError_t launch_from_u128(const unsigned long long *normsq128, const unsigned long long *sq128, int32_t n,
                              int F, double *normsq, double *inv_norm, double *newsq, cudaStream_t st);

@@ -457,6 +457,77 @@ __global__ void __launch_bounds__(UPD_HEAVY_THREADS) k_upd_heavy(UpdateArgs u) {
     update_flush<WRITE>(u, agg);
 }
 
+// ------------------------------------------------------------------------------------
+// Very frequent terms (more than UPD_VH postings; in the tweets-like collection the most
+// frequent term is in half of the documents): one block per chunk of UPD_VCH postings
+// sums its chunk into a shared accumulator over the moved list, tile by tile, and adds the
+// touched entries to vh_sum with 64-bit integer atomics (exact, order-free). The passes
+// then visit the (term, moved position) entries of vh_sum in parallel, so that no single
+// block walks a whole term's postings.
+// ------------------------------------------------------------------------------------
+constexpr int UPD_VH = 8 * UPD_CHUNK;
+constexpr int UPD_VCH = 2 * UPD_CHUNK;
+
+__global__ void __launch_bounds__(UPD_HEAVY_THREADS) k_upd_vh_sum(UpdateArgs u) {
+    extern __shared__ unsigned long long acc[];                              // [UPD_TILE]
+    int32_t *touched = reinterpret_cast<int32_t *>(acc + UPD_TILE);          // [UPD_TILE]
+    __shared__ int32_t n_touched;
+    for (int q = threadIdx.x; q < UPD_TILE; q += UPD_HEAVY_THREADS) acc[q] = 0ull;
+    if (threadIdx.x == 0) n_touched = 0;
+    __syncthreads();
+    for (int c = blockIdx.x; c < u.n_vch; c += gridDim.x) {
+        const int32_t h = u.vch_h[c];
+        const int64_t pb = u.vch_p0[c], pe = u.vch_p1[c];
+        unsigned long long *dst = u.vh_sum + (int64_t)h * u.n_moved;
+        for (int m0 = 0; m0 < u.n_moved; m0 += UPD_TILE) {
+            const int mt = min(UPD_TILE, u.n_moved - m0);
+            for (int64_t p = pb + threadIdx.x; p < pe; p += UPD_HEAVY_THREADS) {
+                const int mm = __ldg(u.mdoc + __ldg(u.row_idx + p)) - m0;
+                if (mm < 0 || mm >= mt) continue;
+                const unsigned long long q = fixed_point(__ldg(u.cval + p), u.F);
+                if (q != 0ull && atomicAdd(acc + mm, q) == 0ull) touched[atomicAdd(&n_touched, 1)] = mm;
+            }
+            __syncthreads();
+            const int nt = n_touched;
+            for (int e = threadIdx.x; e < nt; e += UPD_HEAVY_THREADS) {
+                const int mm = touched[e];
+                atomicAdd(dst + m0 + mm, acc[mm]);
+                acc[mm] = 0ull;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) n_touched = 0;
+            __syncthreads();
+        }
+    }
+}
+
+template <bool WRITE>
+__global__ void __launch_bounds__(256) k_upd_vh_pass(UpdateArgs u) {
+    extern __shared__ unsigned long long agg[];   // [2 * UPD_AGG]
+    for (int q = threadIdx.x; q < 2 * UPD_AGG; q += blockDim.x) agg[q] = 0ull;
+    __syncthreads();
+    const int64_t n = (int64_t)u.n_vh * u.n_moved;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long S = u.vh_sum[e];
+        if (!S) continue;
+        const int64_t h = e / u.n_moved;
+        update_entry<WRITE>(u, __ldg(u.vh_terms + h), (int)(e - h * u.n_moved), S, agg);
+    }
+    __syncthreads();
+    update_flush<WRITE>(u, agg);
+}
+
+cudaError_t launch_update_vh_sums(const UpdateArgs &u, cudaStream_t st) {
+    if (u.n_moved <= 0 || u.n_vh <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(u.vh_sum, 0, sizeof(unsigned long long) * (size_t)u.n_vh * u.n_moved, st);
+    if (e != cudaSuccess) return e;
+    const size_t smem = (size_t)UPD_TILE * (sizeof(unsigned long long) + sizeof(int32_t));
+    e = cudaFuncSetAttribute(k_upd_vh_sum, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_upd_vh_sum<<<min(u.n_vch, 152 * 2), UPD_HEAVY_THREADS, smem, st>>>(u);
+    return cudaGetLastError();
+}
+
 static cudaError_t launch_update(const UpdateArgs &u, bool write, cudaStream_t st) {
     if (u.n_moved <= 0) return cudaSuccess;
     cudaError_t e;
@@ -474,6 +545,14 @@ static cudaError_t launch_update(const UpdateArgs &u, bool write, cudaStream_t s
             if (e != cudaSuccess) return e;
             k_upd_light<false><<<grid, UPD_LIGHT_THREADS, smem_l, st>>>(u);
         }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (u.n_vh > 0) {
+        const int64_t n = (int64_t)u.n_vh * u.n_moved;
+        const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+        if (write) k_upd_vh_pass<true><<<grid, 256, agg_bytes, st>>>(u);
+        else k_upd_vh_pass<false><<<grid, 256, agg_bytes, st>>>(u);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -497,6 +576,8 @@ static cudaError_t launch_update(const UpdateArgs &u, bool write, cudaStream_t s
 cudaError_t launch_update_norm(const UpdateArgs &u, cudaStream_t st) { return launch_update(u, false, st); }
 cudaError_t launch_update_write(const UpdateArgs &u, cudaStream_t st) { return launch_update(u, true, st); }
 int update_chunk_postings() { return UPD_CHUNK; }
+int update_vh_postings() { return UPD_VH; }
+int update_vh_chunk() { return UPD_VCH; }
 
 // normsq[m] = ||S_m||^2 and inv_norm[m] = 1 / ||S_m|| from the 128-bit fixed-point sums
 // (units 2^-2F); newsq[m] from the 128-bit sums of c^2 (units 2^-62).
