@@ -364,3 +364,23 @@ def test_memory_budget_is_enforced(skm):
         with pytest.raises(skm.SkmError) as e:
             km.fit(docs, np.arange(20))
         assert e.value.status == skm.SKM_ERR_BUDGET
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_fit_with_very_frequent_terms_matches_oracle(skm, precision):
+    """Terms with more than 32,768 postings are summed in chunks by many blocks (the update's
+    split path); two terms here exceed that, 22 more take the one-block heavy path. The fit
+    must equal the oracle's."""
+    docs = synth.make_corpus(90000, 20000, 10, 2, 60, 1.05, 4242)
+    df = np.bincount(docs.col_idx, minlength=docs.n_terms)
+    assert (df > 32768).sum() >= 2
+    k = 60
+    ids = synth.init_ids(docs.n_docs, k, 4243)
+    ref = oracle.fit(docs, k, ids, 12)
+    with skm.SphericalKMeans(k, precision=precision, prune="ncc", max_iter=12) as km:
+        r = km.fit(docs, ids)
+        C = km.centroids()
+    assert r.iters == ref.iters
+    np.testing.assert_array_equal(r.assign, ref.a)
+    np.testing.assert_allclose(r.objective, ref.objective, rtol=OBJ_RTOL, atol=0)
+    assert np.abs(C - ref.C).max() < CENT_ATOL
