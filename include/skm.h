@@ -95,7 +95,7 @@ typedef struct {
                                did not change, only against changed ones, Sec. 3.1); every
                                other centroid has similarity below lambda ||x|| <= b. Results
                                are those of the unindexed loop. Used for k <= 16384, for
-                               documents of at most 64 nonzeros with at most
+                               documents of at most 40 nonzeros with at most
                                index_max_cands candidates; the others are scored densely. */
     int32_t index_min_changed; /* the index serves a step only when more than this many
                                   centroids changed in the previous update (Sec. 4.3
@@ -227,7 +227,7 @@ SKM_API skm_status skm_init_kmeanspp(skm_ctx *ctx, const skm_csr *docs, const do
  * c_jt is in P_lambda with minimum overlap count m (a lower bound of the paper's count,
  * clamped to 255), the document shares at least min(m, 255) terms with centroid j. Every
  * centroid with x_i . c_j >= lambda ||x_i|| is a candidate (Lemma 3.1), and so is every
- * candidate of the paper's exact construction. Documents with more than 64 nonzeros are
+ * candidate of the paper's exact construction. Documents with more than 40 nonzeros are
  * not indexed (skm_fit scores them densely): every centroid is reported for them.
  * docs:  as for skm_assign (n_terms = the resident vocabulary).
  * bits:  host uint32[n_docs * ceil(k / 32)]; bit b of bits[i * ceil(k / 32) + w] is set when

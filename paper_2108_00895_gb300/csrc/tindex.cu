@@ -43,14 +43,17 @@ namespace skm {
 
 constexpr int TI_WARPS = 8;
 
-constexpr int TI_STAGE = 64;   // most nonzeros of a document the query serves
+constexpr int TI_STAGE = 40;   // most nonzeros of a document the query serves
 constexpr int TI_CAND = 256;   // most candidates it scores
 constexpr int TI_WALK = 8;     // list entries a lane loads at a time
+constexpr int TI_CGRP = 2;     // bitmap words a lane counts at a time
 constexpr int TI_WALK_RATIO = 16;   // automatic mode: walks above nnz k / 16 entries go dense
 
 // Shared-memory words of one query warp (layout in ti_warp_smem), a multiple of 4 words.
+// The candidate list reuses the count planes (dead after the walk) when they are large enough.
 __host__ __device__ constexpr int64_t ti_warp_words(int32_t W) {
-    return ((int64_t)7 * TI_STAGE + 4 + TI_CAND + (int64_t)(TI_PLANES + 1) * W + 3) & ~int64_t(3);
+    return ((int64_t)7 * TI_STAGE + 4 + ((int64_t)TI_PLANES * W >= TI_CAND ? 0 : TI_CAND) +
+            (int64_t)(TI_PLANES + 1) * W + 3) & ~int64_t(3);
 }
 
 // m bucket: 0 for m = 1, b for m in (2^(b-1), 2^b], TI_MB - 1 for m > 2^(TI_MB - 2).
@@ -325,7 +328,7 @@ __global__ void __launch_bounds__(TI_FILL_WARPS * 32) k_ti_fill(const float *C, 
 // ------------------------------------------------------------------------------------
 // Query: one warp per listed document (grid-stride). A document of at most TI_STAGE
 // nonzeros is staged in shared memory, and every phase issues its loads in independent
-// batches (the baseline's entries, the bitmap words of 4 words x 8 terms at a time, 8 list
+// batches (the baseline's entries, the bitmap words of 2 words x 8 terms at a time, 8 list
 // entries at a time, a candidate's entries for 8 terms at a time), so that a warp waits for a
 // few memory round trips per document rather than one per term.
 // Shared memory per warp (32-bit words): the staged terms, values and baseline entries,
@@ -375,7 +378,7 @@ struct TiWarpSmem {
     uint32_t *pre;  // [TI_STAGE + 1]
     uint32_t *pl;   // [8 W]
     uint32_t *cb;   // [W]
-    int32_t *cl;    // [TI_CAND]
+    int32_t *cl;    // [TI_CAND], over the planes when they hold as many words
 };
 
 __device__ __forceinline__ TiWarpSmem ti_warp_smem(uint32_t *base, int W) {
@@ -393,9 +396,12 @@ __device__ __forceinline__ TiWarpSmem ti_warp_smem(uint32_t *base, int W) {
     q += TI_STAGE;
     s.pre = q;
     q += TI_STAGE + 4;
-    s.cl = reinterpret_cast<int32_t *>(q);
-    q += TI_CAND;
     s.pl = q;
+    if ((int64_t)TI_PLANES * W >= TI_CAND) {
+        s.cl = reinterpret_cast<int32_t *>(q);
+    } else {
+        s.cl = reinterpret_cast<int32_t *>(q + TI_PLANES * W + W);
+    }
     q += TI_PLANES * W;
     s.cb = q;
     return s;
@@ -412,7 +418,7 @@ __device__ __forceinline__ void ti_fallback(const TiQueryArgs &a, int32_t i, int
     }
 }
 
-__global__ void __launch_bounds__(TI_WARPS * 32) k_ti_query(TiQueryArgs a) {
+__global__ void __launch_bounds__(TI_WARPS * 32, 4) k_ti_query(TiQueryArgs a) {
     extern __shared__ __align__(16) uint32_t ti_sm[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -486,11 +492,11 @@ __global__ void __launch_bounds__(TI_WARPS * 32) k_ti_query(TiQueryArgs a) {
             sm.off[p] = __ldg(a.gptr + t);
             sm.len[p] = __ldg(pbe + (int64_t)t * TI_MB);
         }
-        // overlap counts: bit-sliced 8-bit counters (nnz <= 64 < 256), lane-owned words in
-        // groups of 4, kept in shared memory between term batches of 8; a group's 32 bitmap
-        // words are loaded before any is added, 8 at a time by a carry-save adder tree
-        for (int w0 = lane; w0 < W; w0 += 32 * 4) {
-            for (int u = 0; u < 4; ++u) {
+        // overlap counts: bit-sliced 8-bit counters (nnz <= TI_STAGE < 256), lane-owned words
+        // in groups of 2, kept in shared memory between term batches of 8; a group's 16
+        // bitmap words are loaded before any is added, 8 at a time by a carry-save adder tree
+        for (int w0 = lane; w0 < W; w0 += 32 * TI_CGRP) {
+            for (int u = 0; u < TI_CGRP; ++u) {
                 const int w = w0 + 32 * u;
                 if (w < W) {
                     uint4 *v = reinterpret_cast<uint4 *>(sm.pl + TI_PLANES * w);
@@ -500,16 +506,16 @@ __global__ void __launch_bounds__(TI_WARPS * 32) k_ti_query(TiQueryArgs a) {
                 }
             }
             for (int p0 = 0; p0 < nnz; p0 += 8) {
-                uint32_t g[4][8];
+                uint32_t g[TI_CGRP][8];
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
+                for (int u = 0; u < TI_CGRP; ++u)
 #pragma unroll
                     for (int v = 0; v < 8; ++v) {
                         const int w = w0 + 32 * u;
                         g[u][v] = (w < W && p0 + v < nnz) ? __ldg(a.G + (int64_t)sm.t[p0 + v] * W + w) : 0u;
                     }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < TI_CGRP; ++u) {
                     const int w = w0 + 32 * u;
                     if (w >= W) break;
                     uint32_t c[TI_PLANES];

@@ -58,7 +58,7 @@ def test_candidates_contain_oracle_candidates_and_every_high_similarity(skm, sha
     S = oracle.scores(docs, C)
     xn = np.sqrt(np.add.reduceat(docs.values.astype(np.float64) ** 2, docs.row_ptr[:-1]))
     overlap = oracle.scores(docs, (C != 0).astype(np.float32)) > 0   # shares a nonzero term
-    short = np.diff(docs.row_ptr) <= 64     # longer documents are not indexed
+    short = np.diff(docs.row_ptr) <= 40     # longer documents are not indexed
     with skm.SphericalKMeans(w.k, prune="ncc_index") as km:
         km.set_centroids(C)
         for level, lam in enumerate(LAMBDAS):
@@ -66,7 +66,7 @@ def test_candidates_contain_oracle_candidates_and_every_high_similarity(skm, sha
             ref = _as_matrix(oracle.index_candidates(docs, C.astype(np.float64), lam), w.k)
             assert not (ref & ~gpu).any(), f"lambda {lam}: oracle candidate missing"
             assert not ((S >= lam * xn[:, None]) & ~gpu).any(), f"lambda {lam}: high similarity missing"
-            assert gpu[~short].all(), "documents over 64 nonzeros report every centroid"
+            assert gpu[~short].all(), "documents over 40 nonzeros report every centroid"
             gpu, ref = gpu[short], ref[short]
             assert not (gpu & ~overlap[short]).any(), f"lambda {lam}: candidate without a shared term"
             # the value-bin bound stays close to the exact counts
