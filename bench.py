@@ -292,22 +292,30 @@ def run_ours(args, w, world, rank, local, dist):
     docs_done = sum_over_ranks(dist, float(N * iters), dev)
     value = docs_done / (t_max / 1e3)
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: the CSR and the assignment live in
+    # pinned host memory, so that the library's copies run at DMA speed
     e2e = None
     if not args.no_e2e:
-        a_host = np.empty(N, np.int32)
+        from paper_2108_00895_gb300 import synth
+
+        def pinned(x):
+            return torch.from_numpy(np.ascontiguousarray(x)).pin_memory().numpy()
+
+        docs_h = synth.Csr(pinned(docs.row_ptr), pinned(docs.col_idx), pinned(docs.values), docs.n_terms)
+        a_host = torch.empty(N, dtype=torch.int32).pin_memory().numpy()
         barrier(dist)
         t0 = time.perf_counter()
         e_iters = 0
         for _ in range(args.steps):
-            r = km.fit(docs, ids, assign_out=a_host)
+            r = km.fit(docs_h, ids, assign_out=a_host)
             e_iters += r.iters
         dt = time.perf_counter() - t0
         dt = max_over_ranks(dist, dt, dev)
         e_docs = sum_over_ranks(dist, float(N * e_iters), dev)
         e2e = {"value": e_docs / dt, "unit": UNIT,
                "h2d_bytes_per_step": int(8 * (N + 1) + 8 * docs.nnz),
-               "d2h_bytes_per_step": int(4 * N + 8 * (e_iters // max(args.steps, 1)))}
+               "d2h_bytes_per_step": int(4 * N + 8 * (e_iters // max(args.steps, 1))),
+               "host_memory": "pinned"}
 
     pk = peaks()
     fl = 2.0 * agg["fmas_exec"]          # multiply-adds the scoring passes executed
@@ -397,13 +405,21 @@ def run_batched(args, world, rank, local, dist):
     docs_done = sum_over_ranks(dist, float(n_total * W.max_iter * args.steps), dev)
     e2e = None
     if not args.no_e2e:
+        from paper_2108_00895_gb300 import synth
+
+        def pinned(x):
+            return torch.from_numpy(np.ascontiguousarray(x)).pin_memory().numpy()
+
+        # the instances' CSR arrays in pinned host memory (copied before the timed region)
+        inst_h = [(synth.Csr(pinned(d.row_ptr), pinned(d.col_idx), pinned(d.values), d.n_terms), k_, ids_)
+                  for d, k_, ids_ in inst]
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            skm.fit_batched(inst, W.max_iter, tau=args.tau, use_graph=True, tune_cache=cache, device=local)
+            skm.fit_batched(inst_h, W.max_iter, tau=args.tau, use_graph=True, tune_cache=cache, device=local)
         e_dt = max_over_ranks(dist, time.perf_counter() - t0, dev)
         e2e = {"value": docs_done / e_dt, "unit": UNIT,
                "h2d_bytes_per_step": int(sum(8 * (d.n_docs + 1) + 8 * d.nnz for d, _, _ in inst)),
-               "d2h_bytes_per_step": int(4 * n_total + 8 * W.max_iter * len(inst))}
+               "d2h_bytes_per_step": int(4 * n_total + 8 * W.max_iter * len(inst)), "host_memory": "pinned"}
     pk = peaks()
     ach = 2.0 * fmas / (loop_ms / 1e3) / 1e12 if loop_ms > 0 else None
     cpu = None
