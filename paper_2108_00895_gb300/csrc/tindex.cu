@@ -12,29 +12,31 @@
 // GPU form:
 //   G        a term-major bitmap, word w of row t holds the nonzero flags of centroids
 //            32w .. 32w + 31; a document's overlap counts are bit-sliced 8-bit counters
-//            over the words of its terms' rows (k / 8 bytes read per term), saturating at
-//            255 for documents with more nonzeros.
+//            over the words of its terms' rows (k / 8 bytes read per term). The update
+//            keeps G current (it clears and sets the bits of the entries it rewrites).
 //   m bound  instead of sorting each centroid, its entries are counted in 512 bins of |value|
-//            (16 per octave: the float bits >> 19). For an entry in bin b, the entries from
-//            its rank on are bounded above by the bins' upper edges: the entry's own bin
-//            counted whole, then the lower bins. The smallest count whose bounded squares
-//            reach lambda^2 is a lower bound of m_p, so the candidates are a superset of the
-//            paper's; an entry whose bounded tail cannot reach lambda^2 is left out of
-//            P_lambda, as the paper leaves out the entries after it stops. m is stored
-//            clamped to 255 (8 bits), which again only adds candidates.
+//            (16 per octave: the float bits >> 19; the update keeps these counts current
+//            too). For an entry in bin b, the entries from its rank on are bounded above by
+//            the bins' upper edges: the entry's own bin counted whole, then the lower bins.
+//            The smallest count whose bounded squares reach lambda^2 is a lower bound of
+//            m_p, so the candidates are a superset of the paper's; an entry whose bounded
+//            tail cannot reach lambda^2 is left out of P_lambda, as the paper leaves out the
+//            entries after it stops. m is stored clamped to 255 (8 bits), which again only
+//            adds candidates.
 //   P_lambda term-major lists of (centroid << 8 | m), one set of lists per lambda, each term's
 //            list at the offset of its row in G's nonzero count (capacity |G_t| per level),
 //            ordered by m in 8 buckets of doubling width, so that a document walks only the
 //            entries whose m its number of terms can reach.
-//   query    one warp per document: the baseline x . c_{a_old} (FP64), the largest lambda
-//            below it (scaled by ||x||), the overlap counts, the walk of P_lambda over the
-//            document's terms, and FP64 scores of the candidates over the terms where G says
-//            the centroid is nonzero, in CSR order with one fused multiply-add per term
-//            (skipped terms contribute exact zeros, so the sum equals the full CSR-order
-//            sum). Combined with Sec. 3.1: a document whose cluster did not change keeps only
+//   query    one warp per document of at most TI_STAGE nonzeros: the baseline x . c_{a_old}
+//            (FP64), the largest lambda below it (scaled by ||x||), the overlap counts, the
+//            walk of P_lambda over the document's terms, and FP64 scores of the candidates
+//            over the document's terms in CSR order with one fused multiply-add per term
+//            (zero entries add exactly nothing, so the sum equals the full CSR-order sum).
+//            Combined with Sec. 3.1: a document whose cluster did not change keeps only
 //            candidates that changed.
-//   Documents without a threshold below their baseline are appended to the lists of the
-//   dense passes, classified as the Sec. 3.1 partition does.
+//   Documents that the index does not decide (no threshold below the baseline, too long, or
+//   too costly by the rules at k_ti_query) are appended to the lists of the dense passes,
+//   classified as the Sec. 3.1 partition does.
 #include <cmath>
 
 #include "skm_kernels.cuh"
