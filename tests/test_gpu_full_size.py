@@ -103,3 +103,29 @@ def test_pruned_equals_full_at_full_size(skm, name):
     np.testing.assert_array_equal(r_n.objective, r_f.objective)
     np.testing.assert_array_equal(C_n, C_f)
     assert r_n.stats["docs_pruned"] > 0
+
+
+def test_index_equals_ncc_at_full_size(skm):
+    """The threshold index (automatic rules) at the tweets-like analog, N = 1M, d = 783,304,
+    k = 5000, the paper's stop rule: same assignments, objectives and (sampled) centroid
+    columns as the NCC fit."""
+    import torch
+    w = workloads.TWEETS
+    docs = w.corpus()
+    ids = w.init_ids()
+    dev = _device(docs)
+    out = {}
+    for prune in ("ncc", "ncc_index"):
+        with skm.SphericalKMeans(w.k, precision=w.precision, prune=prune, max_iter=w.max_iter,
+                                 shift_tol=w.shift_tol, tau=1e-4) as km:
+            r = km.fit(dev, ids, n_terms=docs.n_terms)
+            cols = synth.sample_ids(w.k, 64, 33)
+            C = km.centroids()[:, cols]
+        torch.cuda.synchronize()
+        out[prune] = (r.assign.cpu().numpy(), r, C)
+    (a_n, r_n, C_n), (a_i, r_i, C_i) = out["ncc"], out["ncc_index"]
+    assert r_i.iters == r_n.iters
+    np.testing.assert_array_equal(a_i, a_n)
+    np.testing.assert_array_equal(r_i.objective, r_n.objective)
+    np.testing.assert_array_equal(C_i, C_n)
+    assert r_i.stats["index_docs"] > 0
