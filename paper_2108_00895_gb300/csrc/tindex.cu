@@ -495,39 +495,36 @@ __global__ void __launch_bounds__(TI_WARPS * 32, 4) k_ti_query(TiQueryArgs a) {
             sm.len[p] = __ldg(pbe + (int64_t)t * TI_MB);
         }
         // overlap counts: bit-sliced 8-bit counters (nnz <= TI_STAGE < 256), lane-owned words
-        // in groups of 2, kept in shared memory between term batches of 8; a group's 16
-        // bitmap words are loaded before any is added, 8 at a time by a carry-save adder tree
+        // in groups of 2 kept in registers over all terms; a batch's 16 bitmap words (2 words
+        // x 8 terms) are loaded before any is added, 8 at a time by a carry-save adder tree
         for (int w0 = lane; w0 < W; w0 += 32 * TI_CGRP) {
+            uint32_t c[TI_CGRP][TI_PLANES];
+#pragma unroll
+            for (int u = 0; u < TI_CGRP; ++u)
+#pragma unroll
+                for (int q = 0; q < TI_PLANES; ++q) c[u][q] = 0u;
+            for (int p0 = 0; p0 < nnz; p0 += 8) {
+                uint32_t g[TI_CGRP][8];
+#pragma unroll
+                for (int v = 0; v < 8; ++v) {
+                    const int64_t row = p0 + v < nnz ? (int64_t)sm.t[p0 + v] * W : -1;
+#pragma unroll
+                    for (int u = 0; u < TI_CGRP; ++u) {
+                        const int w = w0 + 32 * u;
+                        g[u][v] = (w < W && row >= 0) ? __ldg(a.G + row + w) : 0u;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < TI_CGRP; ++u) ti_add8(c[u], g[u]);
+            }
+#pragma unroll
             for (int u = 0; u < TI_CGRP; ++u) {
                 const int w = w0 + 32 * u;
                 if (w < W) {
                     uint4 *v = reinterpret_cast<uint4 *>(sm.pl + TI_PLANES * w);
-                    v[0] = make_uint4(0u, 0u, 0u, 0u);
-                    v[1] = make_uint4(0u, 0u, 0u, 0u);
+                    v[0] = make_uint4(c[u][0], c[u][1], c[u][2], c[u][3]);
+                    v[1] = make_uint4(c[u][4], c[u][5], c[u][6], c[u][7]);
                     sm.cb[w] = 0u;
-                }
-            }
-            for (int p0 = 0; p0 < nnz; p0 += 8) {
-                uint32_t g[TI_CGRP][8];
-#pragma unroll
-                for (int u = 0; u < TI_CGRP; ++u)
-#pragma unroll
-                    for (int v = 0; v < 8; ++v) {
-                        const int w = w0 + 32 * u;
-                        g[u][v] = (w < W && p0 + v < nnz) ? __ldg(a.G + (int64_t)sm.t[p0 + v] * W + w) : 0u;
-                    }
-#pragma unroll
-                for (int u = 0; u < TI_CGRP; ++u) {
-                    const int w = w0 + 32 * u;
-                    if (w >= W) break;
-                    uint32_t c[TI_PLANES];
-                    uint4 *v = reinterpret_cast<uint4 *>(sm.pl + TI_PLANES * w);
-                    const uint4 lo = v[0], hi = v[1];
-                    c[0] = lo.x; c[1] = lo.y; c[2] = lo.z; c[3] = lo.w;
-                    c[4] = hi.x; c[5] = hi.y; c[6] = hi.z; c[7] = hi.w;
-                    ti_add8(c, g[u]);
-                    v[0] = make_uint4(c[0], c[1], c[2], c[3]);
-                    v[1] = make_uint4(c[4], c[5], c[6], c[7]);
                 }
             }
         }
