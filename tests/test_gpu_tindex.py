@@ -160,6 +160,8 @@ def test_invalid_index_arguments(skm):
     for bad in ([0.5, 0.25], [0.0], [1.5], [0.1] * 5):
         with pytest.raises((skm.SkmError, ValueError)):
             skm.SphericalKMeans(8, prune="ncc_index", index_lambdas=bad)
+    with pytest.raises(skm.SkmError):
+        skm.SphericalKMeans(8, prune="ncc_index", index_max_cands=-1)
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
