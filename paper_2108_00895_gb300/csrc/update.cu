@@ -17,6 +17,7 @@
 // S_j . c_j(old) comes from per-document FP64 dots against the old master (k_doc_obj),
 // summed per cluster in fixed point, before the update overwrites it.
 #include <algorithm>
+#include <cstdlib>
 
 #include "skm_device.cuh"
 #include "skm_kernels.cuh"
@@ -576,8 +577,14 @@ static cudaError_t launch_update(const UpdateArgs &u, bool write, cudaStream_t s
 cudaError_t launch_update_norm(const UpdateArgs &u, cudaStream_t st) { return launch_update(u, false, st); }
 cudaError_t launch_update_write(const UpdateArgs &u, cudaStream_t st) { return launch_update(u, true, st); }
 int update_chunk_postings() { return UPD_CHUNK; }
-int update_vh_postings() { return UPD_VH; }
-int update_vh_chunk() { return UPD_VCH; }
+// SKM_UPD_VH / SKM_UPD_VCH override the split threshold and chunk size (tuning).
+static int env_or(const char *name, int dflt) {
+    const char *e = getenv(name);
+    const int v = e ? atoi(e) : 0;
+    return v > 0 ? v : dflt;
+}
+int update_vh_postings() { return env_or("SKM_UPD_VH", UPD_VH); }
+int update_vh_chunk() { return env_or("SKM_UPD_VCH", UPD_VCH); }
 
 // normsq[m] = ||S_m||^2 and inv_norm[m] = 1 / ||S_m|| from the 128-bit fixed-point sums
 // (units 2^-2F); newsq[m] from the 128-bit sums of c^2 (units 2^-62).
