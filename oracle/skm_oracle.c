@@ -549,9 +549,9 @@ int32_t oracle_fit(int64_t n_docs, const int64_t *row_ptr, const int32_t *col, c
  * nearest seed drawn so far). For unit vectors ||x - c||^2 = 2 (1 - x . c), so the weight
  * of document i is proportional to dist_i = 1 - max over seeds of x_i . x_seed.
  * Readings (the paper does not spell the procedure out):
- *   K1 seed 0 is document floor(u_0 N); dist_i = 1 - x_i . x_s in float, the dot product
- *      accumulated over the document's nonzeros in CSR order with one fused multiply-add
- *      (fmaf, a single rounding) per nonzero;
+ *   K1 seed 0 is document floor(u_0 N); dist_i is computed in double, x_it * x_st summed
+ *      over the document's nonzeros in CSR order (products and sums rounded separately;
+ *      a product of two floats is exact in double);
  *   K2 the weights are integers w_i = floor(max(dist_i, 0) 2^32), 0 for documents already
  *      drawn; seed r is the smallest i whose inclusive prefix sum of w exceeds
  *      T = min(floor(u_r W), W - 1), W = sum of w; with W = 0 it is the smallest document
@@ -561,8 +561,8 @@ int32_t oracle_fit(int64_t n_docs, const int64_t *row_ptr, const int32_t *col, c
  * ------------------------------------------------------------------------------------ */
 int oracle_kmeanspp(int64_t n_docs, const int64_t *row_ptr, const int32_t *col, const float *val,
                     int32_t d, int32_t k, const double *u, int32_t *ids) {
-    float *dist = (float *)malloc(sizeof(float) * (size_t)n_docs);
-    float *seed = (float *)calloc((size_t)d, sizeof(float));   /* dense copy of the newest seed */
+    double *dist = (double *)malloc(sizeof(double) * (size_t)n_docs);
+    double *seed = (double *)calloc((size_t)d, sizeof(double));   /* dense copy of the newest seed */
     unsigned char *drawn = (unsigned char *)calloc((size_t)n_docs, 1);
     if (!dist || !seed || !drawn) {
         free(dist);
@@ -577,18 +577,18 @@ int oracle_kmeanspp(int64_t n_docs, const int64_t *row_ptr, const int32_t *col, 
     drawn[first] = 1;
     for (int32_t r = 1; r < k; ++r) {
         const int64_t s = ids[r - 1];
-        for (int64_t p = row_ptr[s]; p < row_ptr[s + 1]; ++p) seed[col[p]] = val[p];
+        for (int64_t p = row_ptr[s]; p < row_ptr[s + 1]; ++p) seed[col[p]] = (double)val[p];
 #pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n_docs; ++i) {
-            float dot = 0.0f;
-            for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) dot = fmaf(val[p], seed[col[p]], dot);
-            const float dd = 1.0f - dot;
+            double dot = 0.0;
+            for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) dot += (double)val[p] * seed[col[p]];
+            const double dd = 1.0 - dot;
             if (dd < dist[i]) dist[i] = dd;
         }
-        for (int64_t p = row_ptr[s]; p < row_ptr[s + 1]; ++p) seed[col[p]] = 0.0f;
+        for (int64_t p = row_ptr[s]; p < row_ptr[s + 1]; ++p) seed[col[p]] = 0.0;
         uint64_t W = 0;
         for (int64_t i = 0; i < n_docs; ++i)
-            if (!drawn[i] && dist[i] > 0.0f) W += (uint64_t)floor((double)dist[i] * 4294967296.0);
+            if (!drawn[i] && dist[i] > 0.0) W += (uint64_t)floor(dist[i] * 4294967296.0);
         int64_t pick = -1;
         if (W == 0) {
             for (int64_t i = 0; i < n_docs && pick < 0; ++i)
@@ -598,7 +598,7 @@ int oracle_kmeanspp(int64_t n_docs, const int64_t *row_ptr, const int32_t *col, 
             if (T >= W) T = W - 1;
             uint64_t run = 0;
             for (int64_t i = 0; i < n_docs; ++i) {
-                if (!drawn[i] && dist[i] > 0.0f) run += (uint64_t)floor((double)dist[i] * 4294967296.0);
+                if (!drawn[i] && dist[i] > 0.0) run += (uint64_t)floor(dist[i] * 4294967296.0);
                 if (run > T) {
                     pick = i;
                     break;

@@ -340,3 +340,46 @@ def test_kmeanspp_seeds_are_distinct():
     ids = oracle.kmeanspp(docs, 50, u)
     assert len(set(ids.tolist())) == 50
     assert ids.min() >= 0 and ids.max() < docs.n_docs
+
+
+def test_kmeanspp_picks_equal_exact_rational_arithmetic_at_every_boundary():
+    """Brute force in exact rational arithmetic (Python fractions; every float32 value and
+    every product is an exact rational): the weights w_i = floor((1 - x_i . x_s) 2^32) and the
+    second seed for uniforms placed on both sides of every prefix-sum boundary. A pick there
+    changes with a single unit of weight, so a distance computed in float (errors of hundreds
+    of units) fails; double is off by far less than a unit. Boundaries whose exact weight lies
+    within 1e-4 of an integer are skipped, because no finite precision decides them."""
+    from fractions import Fraction
+    docs = synth.make_corpus(24, 40, 8, 3, 16, 1.05, 4711)
+    n = docs.n_docs
+    X = [dict() for _ in range(n)]
+    for i in range(n):
+        for p in range(docs.row_ptr[i], docs.row_ptr[i + 1]):
+            X[i][int(docs.col_idx[p])] = Fraction(float(docs.values[p]))
+    u0 = 0.3
+    s0 = int(np.floor(u0 * n))
+    w, fracs = [], []
+    for i in range(n):
+        dist = 1 - sum(v * X[s0].get(t, 0) for t, v in X[i].items())
+        scaled = dist * 2 ** 32
+        wi = int(scaled // 1) if (i != s0 and dist > 0) else 0
+        w.append(wi)
+        fracs.append(float(scaled - int(scaled // 1)) if wi else 0.5)
+    W = sum(w)
+    cum = np.cumsum(np.array(w, dtype=object))
+    checked = 0
+    for m in range(n):
+        if w[m] == 0 or not (1e-4 < fracs[m] < 1 - 1e-4):
+            continue
+        if any(w[i] and not (1e-4 < fracs[i] < 1 - 1e-4) for i in range(m)):
+            break
+        for T in (int(cum[m]) - 1, int(cum[m])):
+            if T >= W:
+                continue
+            u1 = (T + 0.5) / W
+            assert int(np.floor(u1 * W)) == T
+            exact = next(i for i in range(n) if w[i] and cum[i] > T)
+            ids = oracle.kmeanspp(docs, 2, np.array([u0, u1]))
+            assert ids[0] == s0 and ids[1] == exact
+            checked += 1
+    assert checked >= 10
