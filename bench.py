@@ -46,11 +46,16 @@ LARGE_FULL_PASS_ALG_BYTES = 7.43e9
 METRIC = "docs assigned/s per iteration"
 UNIT = "docs/s"
 FP32_LANES_PER_SM = 128
-N_SM = 152
 SM_MAX_MHZ = 2070.0
 
 
-def peaks() -> dict:
+def device_sm_count(local: int = 0) -> int:
+    """Streaming multiprocessors of the device the benchmark runs on (152 on a GB300)."""
+    import torch
+    return int(torch.cuda.get_device_properties(local).multi_processor_count)
+
+
+def peaks(n_sm: int) -> dict:
     p = {"hbm_gbs": 6800.0, "source": "fallback"}
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -58,9 +63,13 @@ def peaks() -> dict:
             m = json.load(f)
         p = {"hbm_gbs": float(m["hbm_gbs"]), "source": "measured",
              "sm_max_mhz": float(m.get("sm_max_mhz", SM_MAX_MHZ))}
-    # FP32 FMA peak from unit counts and the maximum SM clock: 152 SMs x 128 lanes x 2 flop
+    # FP32 FMA peak from unit counts and the maximum SM clock: SMs (read from the device) x
+    # 128 FP32 lanes x 2 flop
     mhz = p.get("sm_max_mhz", SM_MAX_MHZ)
-    p["fp32_tflops"] = N_SM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    p["n_sm"] = n_sm
+    p["fp32_tflops"] = n_sm * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    p["fp32_source"] = (f"FP32 FMA: {n_sm} SMs (device multiProcessorCount) x {FP32_LANES_PER_SM} lanes x "
+                        f"2 flop x {mhz:g} MHz (derived)")
     return p
 
 
@@ -183,6 +192,36 @@ def oracle_sample_rate(docs, C32: np.ndarray, seed: int, budget_s: float = 15.0)
     oracle.assign(sample, C32)
     dt = time.perf_counter() - t0
     return n / dt, n, dt, oracle.num_threads()
+
+
+def oracle_modes(docs, w, seed: int, n_sample: int = 20000, max_iter: int = 10):
+    """The paper's three CPU methods (Sec. 4.1-4.2, Table 1) as the oracle restates them --
+    Baseline (plain Lloyd), NCC (Sec. 3.1) and NCC+INDEX (Sec. 3.2, thresholds of Sec. 4.1) --
+    each a complete fit of a bounded seeded sample of the workload (n_sample documents, the
+    workload's vocabulary, k = n_sample / 200 clusters: the large workload's 200 documents per
+    cluster), with every host core and with one thread."""
+    import oracle
+    from paper_2108_00895_gb300 import synth
+    n = min(n_sample, docs.n_docs)
+    sample = docs.rows(synth.sample_ids(docs.n_docs, n, seed))
+    k = max(2, min(w.k, n // 200))
+    ids = synth.init_ids(n, k, seed + 1)
+    all_cores = oracle.num_threads()
+    out = {"sample": f"{n} seeded documents of the workload, k = {k}, at most {max_iter} steps, "
+                     f"stop on unchanged assignments", "cores_all": all_cores, "modes": {}}
+    try:
+        for threads in (all_cores, 1):
+            oracle.set_threads(threads)
+            for mode in ("plain", "ncc", "ncc_index"):
+                t0 = time.perf_counter()
+                r = oracle.fit(sample, k, ids, max_iter, mode=mode)
+                dt = time.perf_counter() - t0
+                out["modes"].setdefault(mode, {})[f"threads_{threads}"] = {
+                    "docs_per_s_per_iter": n * r.iters / dt, "seconds": dt, "iters": r.iters,
+                    "sims": int(r.sims.sum())}
+    finally:
+        oracle.set_threads(all_cores)
+    return out
 
 
 def run_reference(args, w, world, rank, dist):
@@ -317,7 +356,7 @@ def run_ours(args, w, world, rank, local, dist):
                "d2h_bytes_per_step": int(4 * N + 8 * (e_iters // max(args.steps, 1))),
                "host_memory": "pinned"}
 
-    pk = peaks()
+    pk = peaks(device_sm_count(local))
     fl = 2.0 * agg["fmas_exec"]          # multiply-adds the scoring passes executed
     default_large = (w.name == workloads_large_name() and args.sparse_div == 0)
     score_s = agg["ms_score"] / 1e3
@@ -331,7 +370,7 @@ def run_ours(args, w, world, rank, local, dist):
                                   f"algorithmic bytes of that launch {LARGE_FULL_PASS_ALG_BYTES:.3g}")
                 if default_large else None,
                 "kernel": "k_score (scoring pass: fused CSR x term-major centroid SpMM + top-4)",
-                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)",
+                "peak_source": pk["fp32_source"],
                 "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": pk["hbm_gbs"],
                         "frac": hbm_gbs / pk["hbm_gbs"] if hbm_gbs else None,
                         "peak_source": f"{pk['source']} copy bandwidth"},
@@ -342,13 +381,26 @@ def run_ours(args, w, world, rank, local, dist):
                                 "update_ms_per_step": agg["ms_update"] / args.steps}}
 
     cpu = None
+    checks = {}
+    C_fin = None
+    if rank == 0 and world == 1 and not (args.no_cpu_baseline and args.no_checks):
+        C_fin = km.centroids()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        C = km.centroids()
-        rate, n, dt, cores = oracle_sample_rate(docs, C, 4242, args.cpu_budget)
+        rate, n, dt, cores = oracle_sample_rate(docs, C_fin, 4242, args.cpu_budget)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{n} seeded documents of the workload, one assignment step (plain FP64 "
-                         f"definition) against the final centroids, {dt:.1f} s"}
+                         f"definition) against the final centroids, {dt:.1f} s",
+               "paper_methods": oracle_modes(docs, w, 4343)}
+    if rank == 0 and world == 1 and not args.no_checks:
+        checks["error_vs_oracle"] = error_vs_oracle(skm, km, w, docs, ids, d_docs, a_dev, C_fin, objectives,
+                                                    args, local, stream)
+    del C_fin
     km.close()
+    if rank == 0 and world == 1 and not args.no_checks:
+        checks["speedup_vs_fp32_full"] = fp32_full_speedup(skm, w, docs, ids, d_docs, args, local, stream, value)
+        if w.name == workloads_large_name() and args.serve_check_seconds > 0:
+            from paper_2108_00895_gb300 import workloads
+            checks["serving"] = serving_session(workloads.SERVING, local, args.serve_check_seconds, args.tau)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -364,7 +416,77 @@ def run_ours(args, w, world, rank, local, dist):
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": int(agg["launches_total"]),
                 "work": {k_: v for k_, v in agg.items()}}
+        line.update(checks)
         print(json.dumps(line), flush=True)
+
+
+def error_vs_oracle(skm, km, w, docs, ids, d_docs, a_dev, C_fin, objectives, args, local, stream):
+    """The timed job's results against the FP64 oracle (outside the timed region):
+    - assignments of a seeded sample of documents against the final centroids (skm_assign):
+      mismatches where the oracle's top-2 margin is at least 1e-5 (the contract: none), and
+      in all;
+    - the final update: sampled populated centroid columns against the oracle's normalised
+      member sums of the job's final assignment (max-abs, FP32 master);
+    - the last step's objective against the oracle's sum over all documents, computed with
+      the centroids that step scored (a deterministic fit one step shorter gives them)."""
+    import oracle
+    from paper_2108_00895_gb300 import synth
+    t0 = time.perf_counter()
+    out = {}
+    sample = docs.rows(synth.sample_ids(docs.n_docs, 4000, 4244))
+    a_g, _ = km.assign(sample)
+    a_or, s1, s2 = oracle.assign(sample, C_fin)
+    clear = (s1 - s2) >= 1e-5
+    out["assign_sample_docs"] = int(sample.n_docs)
+    out["assign_mismatch_clear_margin"] = int(((a_g != a_or) & clear).sum())
+    out["assign_mismatch_all"] = int((a_g != a_or).sum())
+    out["assign_near_ties"] = int((~clear).sum())
+    a_fin = a_dev.cpu().numpy()
+    sizes = np.bincount(a_fin, minlength=w.k)
+    pop = np.nonzero(sizes > 0)[0]
+    cols = pop[synth.sample_ids(len(pop), min(40, len(pop)), 4245)]
+    ref = oracle.centroids_subset(docs, a_fin, cols)
+    out["centroid_max_abs"] = float(np.abs(C_fin[:, cols].astype(np.float64) - ref).max())
+    out["centroid_columns"] = int(len(cols))
+    T = len(objectives) if objectives is not None else 0
+    if T > 1:
+        with skm.SphericalKMeans(w.k, precision=w.precision, prune=w.prune, max_iter=T - 1, shift_tol=w.shift_tol,
+                                 rescore=args.rescore == "on", tau=args.tau, device=local, stream=stream.cuda_stream,
+                                 sparse_div=args.sparse_div, index_min_changed=args.index_min_changed,
+                                 index_max_cands=args.index_max_cands) as k2:
+            r2 = k2.fit(d_docs, ids, n_terms=docs.n_terms)
+            C_prev = k2.centroids() if r2.iters == T - 1 else None
+        if C_prev is not None:
+            obj = oracle.objective(docs, C_prev, a_fin)
+            out["objective_rel_err"] = float(abs(float(objectives[-1]) - obj) / abs(obj))
+            out["objective_step"] = T
+        del C_prev
+    out["contract"] = "assignments exact where margin >= 1e-5; objective 1e-6 relative; centroids 1e-5 max-abs"
+    out["seconds"] = time.perf_counter() - t0
+    return out
+
+
+def fp32_full_speedup(skm, w, docs, ids, d_docs, args, local, stream, value):
+    """The plain FP32 full-comparison path on the same corpus (FP32 centroids, no pruning, no
+    rescoring), a few steps after one warm-up fit, timed with CUDA events on the stream: its
+    documents assigned per second per iteration, and the timed job's value over it."""
+    import torch
+    n_it = 3
+    with skm.SphericalKMeans(w.k, precision="fp32", prune="none", max_iter=n_it, shift_tol=-1.0, rescore=False,
+                             tau=args.tau, device=local, stream=stream.cuda_stream) as kf:
+        kf.fit(d_docs, ids, n_terms=docs.n_terms)
+        torch.cuda.synchronize(local)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = kf.fit(d_docs, ids, n_terms=docs.n_terms)
+        e1.record(stream)
+        torch.cuda.synchronize(local)
+        ms = e0.elapsed_time(e1)
+    rate = docs.n_docs * r.iters / (ms / 1e3)
+    return {"fp32_full_docs_per_s_per_iter": rate, "steps": int(r.iters), "ms": ms,
+            "speedup": value / rate,
+            "path": "FP32 centroids, no pruning, no rescoring; the first steps of a fit from the same documents"}
 
 
 # ------------------------------------------------------------------ batched form
@@ -452,30 +574,29 @@ def run_batched(args, world, rank, local, dist):
 
 
 # ------------------------------------------------------------------ serving form
-def run_serving(args, world, rank, local, dist):
-    """Serving form: open-loop Poisson arrivals against skm_server for a fixed window."""
+def serving_session(W, local: int, window: float, tau: float) -> dict:
+    """Serving form: open-loop Poisson arrivals against skm_server for a fixed window on a
+    resident BF16 centroid set under the workload's device budget. Returns the latency,
+    throughput and admission figures."""
     import math
 
     import torch
 
-    from paper_2108_00895_gb300 import skm, synth, workloads
-    W = workloads.SERVING
+    from paper_2108_00895_gb300 import skm, synth
     dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
-    skm.load()
     pool = W.pool()
     # resident centroids: two Lloyd steps on the pool, loaded into an assignment-only context
     with skm.SphericalKMeans(W.k, precision="bf16", prune="ncc", max_iter=2, allocator="cuda", device=local) as tmp:
         tmp.fit(pool, synth.init_ids(pool.n_docs, W.k, 2000 + W.seed))
         C = tmp.centroids()
     stream = torch.cuda.Stream(dev)
-    resident = skm.SphericalKMeans(W.k, precision="bf16", rescore=True, tau=args.tau, allocator="cuda",
+    resident = skm.SphericalKMeans(W.k, precision="bf16", rescore=True, tau=tau, allocator="cuda",
                                    stream=stream.cuda_stream, device=local)
     resident.set_centroids(C)
     del C
     budget = int(W.budget_gb * (1 << 30))
     srv = skm.Server(resident, budget, n_job_slots=2, max_batch_docs=65536, max_batch_nnz=65536 * 300,
-                     job_precision="bf16", job_prune="ncc", tau=args.tau, device=local)
+                     job_precision="bf16", job_prune="ncc", tau=tau, device=local)
     rng = np.random.default_rng(W.seed)
     rp, col, val = pool.row_ptr, pool.col_idx, pool.values
 
@@ -493,15 +614,15 @@ def run_serving(args, world, rank, local, dist):
     # warm-up: a few requests of each kind
     for t in [srv.submit_assign(assign_req(64)) for _ in range(8)]:
         srv.wait(t)
-    d0, k0, i0 = job_req()
     srv.wait(srv.submit_fit(synth.Csr(rp[:10001], col[:rp[10000]], val[:rp[10000]], pool.n_terms), 64,
                             np.arange(64, dtype=np.int32), 2))
-    window = args.serve_seconds
     clocks = ClockSampler(local)
     clocks.start()
     tickets = []
+    depth = []          # (seconds since start, assignments queued, jobs queued, jobs running)
     t0 = time.perf_counter()
     t_next = 0.0
+    last_probe = -1.0
     while True:
         t_next += rng.exponential(1.0 / W.rate)
         if t_next > window:
@@ -515,6 +636,11 @@ def run_serving(args, world, rank, local, dist):
         else:
             docs, k, ids = job_req()
             tickets.append(("fit", docs.n_docs, srv.submit_fit(docs, k, ids, W.job_iters)))
+        if now - last_probe >= 0.5:
+            st_ = srv.stats()
+            depth.append((round(now, 2), int(st_["assign_queued"]), int(st_["fit_queued"]),
+                          int(st_["jobs_running"])))
+            last_probe = now
     t_submit_end = time.perf_counter() - t0
     lat_a, lat_f, docs_a, done_f, cl_docs, deferred, rejected = [], [], 0, 0, 0, 0, 0
     for kind, n, t in tickets:   # assignments drain within a short grace period
@@ -544,21 +670,37 @@ def run_serving(args, world, rank, local, dist):
     pct = lambda v, q: float(np.percentile(v, q)) if len(v) else None
     n_assign = sum(1 for k_, _, _ in tickets if k_ == "assign")
     n_fit = len(tickets) - n_assign
-    line = {"metric": "serving docs assigned/s; p50/p99 assignment latency (ms)", "value": docs_a / t_drain,
-            "unit": "docs/s", "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": 1e3 * t_drain,
+    return {"window_s": window, "assign_requests": n_assign, "assign_done": len(lat_a),
+            "assign_p50_ms": pct(lat_a, 50), "assign_p99_ms": pct(lat_a, 99),
+            "assign_docs_per_s": docs_a / t_drain,
+            "offered_assign_docs_per_s": sum(n for k_, n, _ in tickets if k_ == "assign") / window,
+            "fit_requests": n_fit, "fit_done": done_f, "fit_deferred_at_end": deferred,
+            "fit_deferred_fraction": deferred / n_fit if n_fit else None,
+            "fit_rejected": rejected, "fit_rejected_fraction": rejected / n_fit if n_fit else None,
+            "fit_p50_ms": pct(lat_f, 50), "fit_p99_ms": pct(lat_f, 99),
+            "clustered_docs_per_s": cl_docs / t_drain, "assign_batches": stats["assign_batches"],
+            "max_batch_docs": stats["max_batch_docs_seen"], "peak_jobs_running": stats["peak_jobs_running"],
+            "queue_depth": depth, "budget_gb": W.budget_gb, "resident_gb": stats["resident_mem"] / 2 ** 30,
+            "submit_seconds": t_submit_end, "drain_seconds": t_drain, "clocks": clk}
+
+
+def run_serving(args, world, rank, local, dist):
+    """Serving form on its own: a window of args.serve_seconds."""
+    import torch
+
+    from paper_2108_00895_gb300 import skm, workloads
+    W = workloads.SERVING
+    torch.cuda.set_device(torch.device("cuda", local))
+    skm.load()
+    sv = serving_session(W, local, args.serve_seconds, args.tau)
+    clk = sv.pop("clocks")
+    line = {"metric": "serving docs assigned/s; p50/p99 assignment latency (ms)", "value": sv["assign_docs_per_s"],
+            "unit": "docs/s", "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": 1e3 * sv["drain_seconds"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": dict(W.describe(), window_s=window, job_slots=2, max_batch_docs=65536),
-            "serving": {"assign_requests": n_assign, "assign_done": len(lat_a),
-                        "assign_p50_ms": pct(lat_a, 50), "assign_p99_ms": pct(lat_a, 99),
-                        "assign_docs_per_s": docs_a / t_drain, "offered_assign_docs_per_s":
-                            sum(n for k_, n, _ in tickets if k_ == "assign") / window,
-                        "fit_requests": n_fit, "fit_done": done_f, "fit_deferred_at_end": deferred,
-                        "fit_rejected": rejected, "fit_p50_ms": pct(lat_f, 50), "fit_p99_ms": pct(lat_f, 99),
-                        "clustered_docs_per_s": cl_docs / t_drain, "assign_batches": stats["assign_batches"],
-                        "max_batch_docs": stats["max_batch_docs_seen"], "peak_jobs_running": stats["peak_jobs_running"],
-                        "submit_seconds": t_submit_end, "drain_seconds": t_drain},
-            "clocks": clk, "e2e": {"value": docs_a / t_drain, "unit": "docs/s",
-                                   "h2d_bytes_per_step": None, "d2h_bytes_per_step": None}}
+            "config": dict(W.describe(), window_s=args.serve_seconds, job_slots=2, max_batch_docs=65536),
+            "serving": sv, "clocks": clk,
+            "e2e": {"value": sv["assign_docs_per_s"], "unit": "docs/s", "h2d_bytes_per_step": None,
+                    "d2h_bytes_per_step": None}}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -576,6 +718,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-checks", action="store_true",
+                    help="skip the untimed checks (error against the oracle, FP32 full path, serving window)")
+    ap.add_argument("--serve-check-seconds", type=float, default=3.0,
+                    help="serving window of the default run's serving check (0 = none)")
     ap.add_argument("--profile-run", action="store_true",
                     help="allow fewer warm-up steps (launch lists under a profiler; not a timed number)")
     ap.add_argument("--precision", choices=["bf16", "fp32"], default=None, help="override the workload's")

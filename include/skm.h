@@ -209,13 +209,14 @@ SKM_API skm_status skm_update(skm_ctx *ctx, const skm_csr *docs, const int32_t *
  *   integer weights w_i = floor(max(1 - max over seeds of x_i . seed, 0) * 2^32) (0 for
  *   documents already drawn) exceeds min(floor(uniforms[r] * W), W - 1), W = sum of the
  *   weights; when W = 0 it is the smallest document not drawn yet.
- * The distances are computed in float, 1 - x . seed with one fused multiply-add per nonzero
- * of the document in CSR order, so the seeds depend only on the documents and the uniforms.
+ * The distances are computed in double, 1 - x . seed with the products (exact for two
+ * floats) added one at a time in the document's CSR order, so the seeds depend only on the
+ * documents and the uniforms.
  * docs:      as for skm_fit (validated, staged when on the host).
  * uniforms:  k host doubles in [0, 1), the procedure's random numbers (caller-owned).
  * ids_out:   k int32 document ids (distinct): device memory if docs->on_device, host otherwise.
  * Errors: SKM_ERR_INVALID (a uniform outside [0, 1), k > n_docs, NULL buffers or invalid
- * documents), SKM_ERR_OOM / SKM_ERR_BUDGET (work buffers: 13 bytes per document, 4 per
+ * documents), SKM_ERR_OOM / SKM_ERR_BUDGET (work buffers: 17 bytes per document, 8 per
  * term), SKM_ERR_CUDA. */
 SKM_API skm_status skm_init_kmeanspp(skm_ctx *ctx, const skm_csr *docs, const double *uniforms,
                                      int32_t *ids_out);
@@ -239,7 +240,11 @@ SKM_API skm_status skm_init_kmeanspp(skm_ctx *ctx, const skm_csr *docs, const do
 SKM_API skm_status skm_index_candidates(skm_ctx *ctx, const skm_csr *docs, int32_t level, uint32_t *bits);
 
 /* Replace the resident centroids with a host or device float[n_terms * k] matrix
- * (term-major). The lower-precision copy is re-derived (round to nearest even). */
+ * (term-major). The lower-precision copy is re-derived (round to nearest even). Every entry
+ * must be finite and non-negative (the method's centroids are normalised sums of non-negative
+ * documents, and the scoring pass's decision rule relies on non-negative products): otherwise
+ * SKM_ERR_INVALID, and the context is left without resident centroids (skm_assign then
+ * returns SKM_ERR_STATE until centroids are set or fitted again). */
 SKM_API skm_status skm_set_centroids(skm_ctx *ctx, int32_t n_terms, const float *centroids,
                              int32_t on_device);
 
@@ -254,6 +259,13 @@ SKM_API skm_status skm_get_stats(const skm_ctx *ctx, skm_stats *out);
 
 /* Device bytes currently held by the context. */
 SKM_API size_t skm_mem_used(const skm_ctx *ctx);
+
+/* The GPU architecture the library's kernels were compiled for, as the CUDA runtime reports
+ * it for the scoring kernel on the current device (cudaFuncAttributes.binaryVersion, major *
+ * 10 + minor: 103 for sm_103a). Needs a CUDA device; SKM_ERR_CUDA otherwise (for example when
+ * the device cannot run the library's code), SKM_ERR_INVALID for a NULL out. No counterpart
+ * in the paper: a check of the build. */
+SKM_API skm_status skm_device_code_version(int32_t *out);
 
 /* ------------------------------------------------------------------------------------
  * Batched form: many independent clustering instances of different sizes in one call.
@@ -390,16 +402,19 @@ SKM_API skm_status skm_server_destroy(skm_server *srv);
  *   k           number of centroids, >= 1.
  *   centroids   device float[n_terms * ld], term-major, 16-byte aligned: entry (t, j) is
  *               centroids[t * ld + j]; ld >= k and a multiple of 256 (columns k..ld-1 are
- *               read and ignored).
+ *               read and ignored). The used entries must be finite and non-negative, as for
+ *               skm_set_centroids; each call checks them on the device (one read of the
+ *               n_terms x k block).
  *   assign_out  device int32[n_docs]; score_out device float[n_docs] (the FP32 similarity of
  *               the chosen centroid) or NULL.
  *   stream      cudaStream_t to run on (NULL = legacy default stream); the call returns after
  *               its work on the stream has finished.
  * Limit: n_docs * ceil(k / 256) <= 1,048,568 (32 bytes of scratch per document and 256-column
  * slice); a larger request returns SKM_ERR_BUDGET before any GPU work.
- * Errors: SKM_ERR_INVALID for bad arguments or documents, SKM_ERR_CUDA for a CUDA failure.
- * The first call on a device looks up the scratch array's device address (once per device,
- * with that device current); make that first call before any stream capture on the device.
+ * Errors: SKM_ERR_INVALID for bad arguments, documents or centroids, SKM_ERR_CUDA for a CUDA
+ * failure. Every call looks up the scratch array's device address on the current device and
+ * copies the validation flags back to the host, then synchronises the stream before it returns:
+ * it must not be called while that stream is being captured into a CUDA graph.
  * All calls share the one scratch array, which keeps the last call's contents: calls that
  * overlap on the GPU (from several streams or threads) race, so the caller must serialise them.
  */

@@ -5,8 +5,6 @@
 // one FP32 fused multiply-add per nonzero per centroid. The chain for a given (i, j) is the
 // same whichever launch computes it (full matrix or compacted moved-centroid matrix), so a
 // score is a pure function of (x_i, c_j): the pruned and the full pass agree bit for bit.
-#include <cstdlib>
-
 #include "skm_device.cuh"
 #include "skm_internal.cuh"
 #include "skm_kernels.cuh"
@@ -91,12 +89,7 @@ int slice_width(int precision, int k, double mean_nnz) {
     // stay few. Short documents (at most 32 nonzeros on average) take the wider FP32 slice:
     // the per-slice top-4 merge then costs as much as their multiply-adds, and a wider
     // slice spreads it over twice the columns (tweets-like k = 5000: scoring -18%; documents
-    // of 120 nonzeros: +12%). SKM_SLICE overrides the choice (tuning).
-    if (const char *env = getenv("SKM_SLICE")) {
-        const int v = atoi(env);
-        if (precision == 0 && (v == 128 || v == 256 || v == 512)) return v;
-        if (precision == 1 && (v == 256 || v == 512 || v == 1024)) return v;
-    }
+    // of 120 nonzeros: +12%).
     if (precision == 0) return k <= 128 ? 128 : (mean_nnz <= 32.0 ? 512 : 256);
     return k <= 256 ? 256 : 512;
 }
@@ -131,6 +124,13 @@ static cudaError_t launch_score_t(const ScoreArgs &a, int precision, int slice_c
     }
 #undef SKM_SCORE
     return cudaGetLastError();
+}
+
+cudaError_t score_kernel_version(int *out) {
+    cudaFuncAttributes fa{};
+    const cudaError_t e = cudaFuncGetAttributes(&fa, k_score<__nv_bfloat16, 2, false>);
+    if (e == cudaSuccess) *out = fa.binaryVersion;
+    return e;
 }
 
 cudaError_t launch_score(const ScoreArgs &a, int precision, int slice_cols, cudaStream_t st, const SparseArgs *sp) {
@@ -205,8 +205,9 @@ __global__ void k_decide(DecideArgs a) {
     int64_t nnz = a.row_ptr[i + 1] - a.row_ptr[i];
     if (s1 <= 0.f && rho <= 0.f) {
         // every score is exactly zero: the document shares no term with any centroid's
-        // support (scores are sums of non-negative products), so every exact score is zero
-        // and the lowest index, centroid 0, is the argmax
+        // support (scores are sums of non-negative products: documents are validated, and
+        // centroids are normalised sums of documents or validated when set from outside), so
+        // every exact score is zero and the lowest index, centroid 0, is the argmax
         a.a_new[i] = 0;
         a.s_state[i] = 0.f;
         a.r_state[i] = 0.f;

@@ -13,8 +13,6 @@
 // multiply-adds), ties to the lowest index.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "skm.h"
 #include "skm_kernels.cuh"
 
@@ -23,29 +21,19 @@ namespace {
 constexpr size_t kScratchBytes = size_t(32) << 20;   // 32 MiB
 constexpr size_t kCounterBytes = 256;                 // validation flags, kept first
 constexpr int kSlice = 256;                           // FP32 scoring slice (columns)
-constexpr int kMaxDevices = 64;
 
 // The scratch. In host code `g_scratch` names a host-side stand-in, not device memory: its
-// device address comes from cudaGetSymbolAddress, taken once per device.
+// device address comes from cudaGetSymbolAddress with the device current.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-std::mutex g_mu;
-void *g_addr[kMaxDevices] = {};
-
-// Device address of g_scratch on the current device (set up on the first call there).
+// Device address of g_scratch on the current device. It is looked up on every call (cheap
+// after the first on a device), so a module reloaded after cudaDeviceReset is not addressed
+// through a stale pointer.
 cudaError_t scratch_address(void **out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess) return e;
-        g_addr[dev] = p;
-    }
-    *out = g_addr[dev];
+    *out = p;
     return cudaSuccess;
 }
 
@@ -94,20 +82,23 @@ extern "C" SKM_API skm_status skm_assign_fixed_scratch(const skm_csr *docs, int3
     float *part_s = reinterpret_cast<float *>(scr + kCounterBytes);
     int32_t *part_j = reinterpret_cast<int32_t *>(part_s + (size_t)n * n_slices * skm::TOPT);
 
-    // row_ptr bounds, then the same device validation as the other entry points
+    // row_ptr bounds, then the same device validation as the other entry points: documents
+    // (flags[0]) and centroids, which must be finite and non-negative as skm_set_centroids
+    // requires (flags[1]; the k used columns of each of the n_terms rows)
     int64_t ends[2] = {-1, -1};
     if (cudaMemcpyAsync(&ends[0], docs->row_ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaMemcpyAsync(&ends[1], docs->row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaMemsetAsync(flags, 0, kCounterBytes, st) != cudaSuccess)
         return SKM_ERR_CUDA;
     if (skm::launch_validate(docs->row_ptr, docs->col_idx, docs->values, n, docs->nnz, docs->n_terms, flags, st) !=
-        cudaSuccess)
+            cudaSuccess ||
+        skm::launch_validate_matrix(centroids, ld, docs->n_terms, k, flags + 1, st) != cudaSuccess)
         return SKM_ERR_CUDA;
-    int32_t err = 0;
-    if (cudaMemcpyAsync(&err, flags, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+    int32_t err[2] = {0, 0};
+    if (cudaMemcpyAsync(err, flags, sizeof err, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return SKM_ERR_CUDA;
-    if (ends[0] != 0 || ends[1] != docs->nnz || err != 0) return SKM_ERR_INVALID;
+    if (ends[0] != 0 || ends[1] != docs->nnz || err[0] != 0 || err[1] != 0) return SKM_ERR_INVALID;
 
     skm::ScoreArgs sa{};
     sa.row_ptr = docs->row_ptr;

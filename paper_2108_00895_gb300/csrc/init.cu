@@ -2,16 +2,18 @@
 // each new seed is drawn with probability proportional to the squared distance to the
 // nearest seed so far, which for unit vectors is 2 (1 - x . seed). One round per seed:
 //   k_pp_scatter  the newest seed into a dense vector of the vocabulary;
-//   k_pp_dist     every document's distance dist_i = min(dist_i, 1 - x_i . seed) in float,
-//                 the dot product accumulated over the document's nonzeros in CSR order with
-//                 one fused multiply-add per nonzero, and its integer weight
+//   k_pp_dist     every document's distance dist_i = min(dist_i, 1 - x_i . seed) in double,
+//                 the products x_it * seed_t (exact: two floats) added one by one in CSR
+//                 order, each addition rounded once, and its integer weight
 //                 w_i = floor(max(dist_i, 0) 2^32) (0 once drawn);
 //   k_pp_chunks   the weight total of each chunk of PP_CHUNK documents;
 //   k_pp_pick     one block: W = sum of the totals, T = min(floor(u W), W - 1), the chunk
 //                 and then the document whose inclusive prefix sum first exceeds T (the
 //                 smallest undrawn document when W = 0); it also clears the seed vector.
 // Integer weights make the prefix sums exact, so the seeds are a deterministic function of
-// the documents and the uniforms, whatever the thread layout.
+// the documents and the uniforms, whatever the thread layout. The distances follow the
+// definition in double (the operation order of a sequential loop over the nonzeros); FP64
+// is the slow pipe of this GPU, which makes a round about twice as long as in float.
 #include <cmath>
 
 #include "skm_internal.cuh"
@@ -22,42 +24,43 @@ constexpr int PP_CHUNK = 8192;
 constexpr int PP_PICK_THREADS = 1024;
 constexpr int PP_PER_THREAD = PP_CHUNK / PP_PICK_THREADS;
 
-__device__ __forceinline__ unsigned long long pp_weight(float dist, uint8_t drawn) {
-    return (!drawn && dist > 0.0f) ? (unsigned long long)floor((double)dist * 4294967296.0) : 0ull;
+__device__ __forceinline__ unsigned long long pp_weight(double dist, uint8_t drawn) {
+    return (!drawn && dist > 0.0) ? (unsigned long long)floor(dist * 4294967296.0) : 0ull;
 }
 
 __global__ void k_pp_scatter(int64_t n, const int32_t *ids, int r, const int64_t *row_ptr, const int32_t *col,
-                             const float *val, float *seed) {
+                             const float *val, double *seed) {
     const int32_t s = ids[r];
     if (s < 0 || s >= n) return;   // a failed draw is reported by the host
-    for (int64_t p = row_ptr[s] + threadIdx.x; p < row_ptr[s + 1]; p += blockDim.x) seed[col[p]] = val[p];
+    for (int64_t p = row_ptr[s] + threadIdx.x; p < row_ptr[s + 1]; p += blockDim.x) seed[col[p]] = (double)val[p];
 }
 
 __global__ void k_pp_dist(int64_t n, const int32_t *order, const int64_t *row_ptr, const int32_t *col,
-                          const float *val, const float *seed, int first, float *dist, const uint8_t *drawn,
+                          const float *val, const double *seed, int first, double *dist, const uint8_t *drawn,
                           unsigned long long *w) {
     const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (pos >= n) return;
     const int64_t i = order ? (int64_t)order[pos] : pos;
     const int64_t pe = row_ptr[i + 1];
-    float dot = 0.f;
+    double dot = 0.0;
     // 8 entries at a time: their loads are in flight together and share cache lines; the
-    // fused multiply-adds still run over the entries in CSR order
+    // additions still run over the entries in CSR order, a product then a sum, each rounded
+    // on its own (no fused multiply-add), as a sequential double loop computes them
     constexpr int B = 8;
     for (int64_t p0 = row_ptr[i]; p0 < pe; p0 += B) {
-        float x[B], c[B];
+        double x[B], c[B];
 #pragma unroll
         for (int q = 0; q < B; ++q) {
             const int64_t p = p0 + q;
-            x[q] = p < pe ? __ldg(val + p) : 0.f;
-            c[q] = p < pe ? __ldg(seed + __ldg(col + p)) : 0.f;
+            x[q] = p < pe ? (double)__ldg(val + p) : 0.0;
+            c[q] = p < pe ? __ldg(seed + __ldg(col + p)) : 0.0;
         }
 #pragma unroll
         for (int q = 0; q < B; ++q)
-            if (p0 + q < pe) dot = __fmaf_rn(x[q], c[q], dot);
+            if (p0 + q < pe) dot = __dadd_rn(dot, __dmul_rn(x[q], c[q]));
     }
-    const float dd = 1.0f - dot;
-    float cur = first ? dd : dist[i];
+    const double dd = __dadd_rn(1.0, -dot);
+    double cur = first ? dd : dist[i];
     if (dd < cur) cur = dd;
     dist[i] = cur;
     w[i] = pp_weight(cur, drawn[i]);
@@ -82,7 +85,7 @@ __global__ void k_pp_chunks(int64_t n, const unsigned long long *w, unsigned lon
 __global__ void __launch_bounds__(PP_PICK_THREADS) k_pp_pick(int64_t n, int32_t nb, const unsigned long long *csum,
                                                              const unsigned long long *w, const double *u, int r,
                                                              int32_t *ids, uint8_t *drawn, const int64_t *row_ptr,
-                                                             const int32_t *col, float *seed) {
+                                                             const int32_t *col, double *seed) {
     __shared__ unsigned long long scan[PP_PICK_THREADS];
     __shared__ unsigned long long s_T, s_base;
     __shared__ int64_t s_c0, s_pick;
@@ -90,7 +93,7 @@ __global__ void __launch_bounds__(PP_PICK_THREADS) k_pp_pick(int64_t n, int32_t 
     // the previous seed's entries of the dense vector are no longer needed
     const int32_t prev = ids[r - 1];
     if (prev >= 0 && prev < n)
-        for (int64_t p = row_ptr[prev] + threadIdx.x; p < row_ptr[prev + 1]; p += blockDim.x) seed[col[p]] = 0.f;
+        for (int64_t p = row_ptr[prev] + threadIdx.x; p < row_ptr[prev + 1]; p += blockDim.x) seed[col[p]] = 0.0;
     if (threadIdx.x == 0) {
         unsigned long long W = 0ull;
         for (int b = 0; b < nb; ++b) W += csum[b];
@@ -162,8 +165,8 @@ __global__ void __launch_bounds__(PP_PICK_THREADS) k_pp_pick(int64_t n, int32_t 
 }
 
 cudaError_t launch_kmeanspp(int64_t n, int32_t d, int32_t k, const int32_t *order, const int64_t *row_ptr,
-                            const int32_t *col, const float *val, const double *u, int32_t *ids, float *dist,
-                            unsigned long long *w, unsigned long long *csum, uint8_t *drawn, float *seed,
+                            const int32_t *col, const float *val, const double *u, int32_t *ids, double *dist,
+                            unsigned long long *w, unsigned long long *csum, uint8_t *drawn, double *seed,
                             cudaStream_t st) {
     (void)d;
     const int32_t nb = (int32_t)((n + PP_CHUNK - 1) / PP_CHUNK);

@@ -1122,11 +1122,11 @@ skm_status skm_init_kmeanspp(skm_ctx *ctx, const skm_csr *docs, const double *un
     DevCsr dc{};
     SKM_TRY(stage_docs(ctx, docs, dc));
     const int64_t n = dc.n;
-    SKM_TRY(ensure(ctx, ctx->pp_dist, sizeof(float) * n));
+    SKM_TRY(ensure(ctx, ctx->pp_dist, sizeof(double) * n));
     SKM_TRY(ensure(ctx, ctx->pp_w, sizeof(unsigned long long) * n));
     SKM_TRY(ensure(ctx, ctx->pp_csum, sizeof(unsigned long long) * kmeanspp_chunks(n)));
     SKM_TRY(ensure(ctx, ctx->pp_drawn, (size_t)n));
-    SKM_TRY(ensure(ctx, ctx->pp_seed, sizeof(float) * dc.d));
+    SKM_TRY(ensure(ctx, ctx->pp_seed, sizeof(double) * dc.d));
     SKM_TRY(ensure(ctx, ctx->pp_ids, sizeof(int32_t) * k));
     SKM_TRY(ensure(ctx, ctx->pp_u, sizeof(double) * k));
     SKM_TRY(ensure_doc_bufs(ctx, n));
@@ -1135,14 +1135,14 @@ skm_status skm_init_kmeanspp(skm_ctx *ctx, const skm_csr *docs, const double *un
     if (first >= n) first = (int32_t)(n - 1);
     const uint8_t one = 1;
     SKM_CUDA(cudaMemsetAsync(ctx->pp_drawn.p, 0, (size_t)n, ctx->st));
-    SKM_CUDA(cudaMemsetAsync(ctx->pp_seed.p, 0, sizeof(float) * dc.d, ctx->st));
+    SKM_CUDA(cudaMemsetAsync(ctx->pp_seed.p, 0, sizeof(double) * dc.d, ctx->st));
     SKM_CUDA(cudaMemcpyAsync(P<uint8_t>(ctx->pp_drawn) + first, &one, 1, cudaMemcpyHostToDevice, ctx->st));
     SKM_CUDA(cudaMemcpyAsync(ctx->pp_ids.p, &first, sizeof(int32_t), cudaMemcpyHostToDevice, ctx->st));
     SKM_CUDA(cudaMemcpyAsync(ctx->pp_u.p, uniforms, sizeof(double) * k, cudaMemcpyHostToDevice, ctx->st));
     SKM_CUDA(launch_order_by_length(dc.row_ptr, n, P<int32_t>(ctx->order_hist), P<int32_t>(ctx->order), ctx->st));
     SKM_CUDA(launch_kmeanspp(n, dc.d, k, P<int32_t>(ctx->order), dc.row_ptr, dc.col, dc.val, P<double>(ctx->pp_u),
-                             P<int32_t>(ctx->pp_ids), P<float>(ctx->pp_dist), P<unsigned long long>(ctx->pp_w),
-                             P<unsigned long long>(ctx->pp_csum), P<uint8_t>(ctx->pp_drawn), P<float>(ctx->pp_seed),
+                             P<int32_t>(ctx->pp_ids), P<double>(ctx->pp_dist), P<unsigned long long>(ctx->pp_w),
+                             P<unsigned long long>(ctx->pp_csum), P<uint8_t>(ctx->pp_drawn), P<double>(ctx->pp_seed),
                              ctx->st));
     std::vector<int32_t> ids(k);
     SKM_CUDA(cudaMemcpyAsync(ids.data(), ctx->pp_ids.p, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, ctx->st));
@@ -1193,6 +1193,17 @@ skm_status skm_prepare_assign(skm_ctx *ctx) {
 int32_t skm_n_terms(const skm_ctx *ctx) { return ctx ? ctx->d : 0; }
 
 size_t skm_mem_used(const skm_ctx *ctx) { return ctx ? ctx->used : 0; }
+
+skm_status skm_device_code_version(int32_t *out) {
+    if (!out) return SKM_ERR_INVALID;
+    int v = 0;
+    if (score_kernel_version(&v) != cudaSuccess) {
+        cudaGetLastError();
+        return SKM_ERR_CUDA;
+    }
+    *out = (int32_t)v;
+    return SKM_OK;
+}
 
 skm_status skm_get_stats(const skm_ctx *ctx, skm_stats *out) {
     if (!ctx || !out) return SKM_ERR_INVALID;
@@ -1497,6 +1508,21 @@ skm_status skm_set_centroids(skm_ctx *ctx, int32_t n_terms, const float *centroi
     SKM_CUDA(cudaMemcpy2DAsync(ctx->C32.p, sizeof(float) * ctx->ldc, centroids, sizeof(float) * k,
                                sizeof(float) * k, n_terms,
                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->st));
+    // every score is a sum of non-negative products (the decision's all-zero rule and error
+    // bounds rest on it): a negative or non-finite entry is rejected and leaves the context
+    // without resident centroids
+    SKM_TRY(reset_counters(ctx));
+    SKM_CUDA(launch_validate_matrix(P<float>(ctx->C32), ctx->ldc, n_terms, k, P<int32_t>(ctx->counters) + CNT_ERR,
+                                    ctx->st));
+    ctx->stats.launches_total++;
+    SKM_TRY(read_counters(ctx));
+    if (ctx->h_counters[CNT_ERR]) {
+        ctx->d = 0;
+        ctx->cent_epoch++;
+        ctx->csupport.clear();
+        ctx->cm_valid = false;
+        return fail(ctx, SKM_ERR_INVALID, "centroids must be finite and non-negative");
+    }
     if (ctx->cfg.precision == SKM_BF16) {
         SKM_CUDA(launch_to_bf16(P<float>(ctx->C32), P<__nv_bfloat16>(ctx->C16), (int64_t)n_terms * ctx->ldc, ctx->st));
         ctx->stats.launches_total++;

@@ -125,6 +125,8 @@ cudaError_t launch_score(const ScoreArgs &a, int precision, int slice_cols, cuda
                          const SparseArgs *sp = nullptr);
 cudaError_t launch_collect(const ScoreArgs &a, int precision, int slice_cols, cudaStream_t st,
                            const SparseArgs *sp = nullptr);
+// cudaFuncAttributes.binaryVersion of the scoring kernel on the current device
+cudaError_t score_kernel_version(int *out);
 // KS for the scoring kernel, given the mean nonzeros of the documents it will score
 int slice_width(int precision, int k, double mean_nnz = 1e9);
 
@@ -147,11 +149,11 @@ cudaError_t launch_rare_fill(const void *M, int precision, int64_t ldc, int32_t 
 cudaError_t launch_mark_rare(const int32_t *col, int64_t nnz, const uint8_t *flag, int32_t *colm, cudaStream_t st);
 
 // k-means++ seeding (defined in init.cu): rounds 1..k-1 given ids[0] on the device, drawn
-// (n bytes) zero except drawn[ids[0]] = 1 and seed (d floats) zero; u: k uniforms on the
+// (n bytes) zero except drawn[ids[0]] = 1 and seed (d doubles) zero; u: k uniforms on the
 // device; dist, w: n entries; csum: kmeanspp_chunks(n) entries. Leaves seed zero.
 cudaError_t launch_kmeanspp(int64_t n, int32_t d, int32_t k, const int32_t *order, const int64_t *row_ptr,
-                            const int32_t *col, const float *val, const double *u, int32_t *ids, float *dist,
-                            unsigned long long *w, unsigned long long *csum, uint8_t *drawn, float *seed,
+                            const int32_t *col, const float *val, const double *u, int32_t *ids, double *dist,
+                            unsigned long long *w, unsigned long long *csum, uint8_t *drawn, double *seed,
                             cudaStream_t st);
 int kmeanspp_chunks(int64_t n);
 

@@ -107,6 +107,11 @@ cudaError_t launch_partition(const PartitionArgs &a, cudaStream_t st);
 cudaError_t launch_validate(const int64_t *row_ptr, const int32_t *col, const float *val,
                             int64_t n_docs, int64_t nnz, int32_t n_terms, int32_t *err, cudaStream_t st);
 
+// Entries of a rows x cols block of M (row stride ld) that are negative or not finite set bit
+// 2 of *err (centroids given from outside).
+cudaError_t launch_validate_matrix(const float *M, int64_t ld, int32_t rows, int32_t cols, int32_t *err,
+                                   cudaStream_t st);
+
 // order[] = document ids by decreasing number of nonzeros; hist is scratch of 4096 ints.
 cudaError_t launch_order_by_length(const int64_t *row_ptr, int64_t n, int32_t *hist, int32_t *order,
                                    cudaStream_t st);

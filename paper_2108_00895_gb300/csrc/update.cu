@@ -66,6 +66,30 @@ cudaError_t launch_validate(const int64_t *row_ptr, const int32_t *col, const fl
     return cudaGetLastError();
 }
 
+// Entries of a row-major rows x cols block (row stride ld) that are negative or not finite
+// set bit 2 of *err. Every score of the method is a sum of non-negative products (tf-idf
+// documents and centroids that are normalised sums of them), which the scoring pass and its
+// decision rely on, so centroids given from outside are checked the same way as documents.
+__global__ void k_validate_matrix(const float *M, int64_t ld, int32_t rows, int32_t cols, int32_t *err) {
+    const int64_t n = (int64_t)rows * cols;
+    int e = 0;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = q / cols, c = q - r * cols;
+        const float v = M[r * ld + c];
+        if (!(v >= 0.f) || !isfinite(v)) e = 2;
+    }
+    if (__any_sync(FULL, e != 0) && (threadIdx.x & 31) == 0) atomicOr(err, 2);
+}
+
+cudaError_t launch_validate_matrix(const float *M, int64_t ld, int32_t rows, int32_t cols, int32_t *err,
+                                   cudaStream_t st) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    const int64_t n = (int64_t)rows * cols;
+    const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16);
+    k_validate_matrix<<<blocks, 256, 0, st>>>(M, ld, rows, cols, err);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------------------------
 // Documents ordered by decreasing number of nonzeros (bucket sort; order within a bucket
 // is arbitrary and affects only scheduling): neighbouring warps of a scoring block then
@@ -577,14 +601,8 @@ static cudaError_t launch_update(const UpdateArgs &u, bool write, cudaStream_t s
 cudaError_t launch_update_norm(const UpdateArgs &u, cudaStream_t st) { return launch_update(u, false, st); }
 cudaError_t launch_update_write(const UpdateArgs &u, cudaStream_t st) { return launch_update(u, true, st); }
 int update_chunk_postings() { return UPD_CHUNK; }
-// SKM_UPD_VH / SKM_UPD_VCH override the split threshold and chunk size (tuning).
-static int env_or(const char *name, int dflt) {
-    const char *e = getenv(name);
-    const int v = e ? atoi(e) : 0;
-    return v > 0 ? v : dflt;
-}
-int update_vh_postings() { return env_or("SKM_UPD_VH", UPD_VH); }
-int update_vh_chunk() { return env_or("SKM_UPD_VCH", UPD_VCH); }
+int update_vh_postings() { return UPD_VH; }
+int update_vh_chunk() { return UPD_VCH; }
 
 // normsq[m] = ||S_m||^2 and inv_norm[m] = 1 / ||S_m|| from the 128-bit fixed-point sums
 // (units 2^-2F); newsq[m] from the 128-bit sums of c^2 (units 2^-62).

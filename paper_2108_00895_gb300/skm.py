@@ -127,7 +127,7 @@ EXPORTS = ("skm_config_default", "skm_create", "skm_destroy", "skm_last_error", 
            "skm_get_stats", "skm_mem_used", "skm_fit_batched", "skm_server_create", "skm_server_submit_assign",
            "skm_server_submit_fit", "skm_server_wait", "skm_server_release", "skm_server_get_stats",
            "skm_server_destroy", "skm_assign_fixed_scratch", "skm_init_kmeanspp",
-           "skm_index_candidates")
+           "skm_index_candidates", "skm_device_code_version")
 
 # skm_assign_fixed_scratch: capacity of its fixed scratch, in (document x 256-column slice) units
 FIXED_SCRATCH_SLICE = 256
@@ -163,6 +163,7 @@ def load(build_if_missing: bool = True):
             "skm_n_terms": (ctypes.c_int32, [P]),
             "skm_get_stats": (st, [P, ctypes.POINTER(skm_stats)]),
             "skm_mem_used": (ctypes.c_size_t, [P]),
+            "skm_device_code_version": (st, [ctypes.POINTER(ctypes.c_int32)]),
             "skm_assign_fixed_scratch": (st, [ctypes.POINTER(skm_csr), ctypes.c_int32, P, ctypes.c_int64,
                                               P, P, P]),
             "skm_fit_batched": (st, [ctypes.POINTER(skm_batch_config), ctypes.POINTER(skm_batch_item),

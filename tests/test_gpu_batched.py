@@ -62,6 +62,35 @@ def test_batched_instances_match_oracle(skm, tmp_path, use_graph):
         np.testing.assert_array_equal(obj, obj2)
 
 
+def test_batched_instances_at_the_workload_extremes_match_oracle(skm, tmp_path):
+    """The batched workload's extremes (k up to 2048, d up to 100,000, tens of thousands of
+    documents, mean 80 nonzeros, Zipf 1.1): the 1024- and 2048-column scoring shapes and the
+    update's heavy and very frequent term paths inside the batched kernels, each instance
+    against a plain oracle fit."""
+    spec = [(60000, 100000, 2048), (30000, 50000, 1024), (12000, 20000, 700), (3000, 20000, 16)]
+    inst = []
+    for q, (n, d, k) in enumerate(spec):
+        docs = synth.make_corpus(n, d, 80, 5, 2000, 1.1, 3100 + q)
+        inst.append((docs, k, synth.init_ids(n, k, 4100 + q)))
+    # two steps: the first update (every heavy-term path) and a second assignment against the
+    # updated centroids; that assignment is compared where the oracle's top-2 margin on the
+    # centroids it was scored against is at least 1e-5 (the FP32 master and the oracle's FP64
+    # centroids can order a closer pair differently)
+    max_iter = 2
+    res, stats = skm.fit_batched(inst, max_iter, tune_cache=str(tmp_path / "tune.txt"))
+    assert stats["message"] == ""
+    for (docs, k, ids), (a, obj) in zip(inst, res):
+        ref = oracle.fit(docs, k, ids, max_iter)
+        C1 = oracle.fit(docs, k, ids, 1).C
+        _, s1, s2 = oracle.assign(docs, C1)
+        clear = (s1 - s2) >= MARGIN
+        assert clear.mean() > 0.9
+        bad = np.nonzero((a != ref.a) & clear)[0]
+        assert len(bad) == 0, f"k = {k}: {len(bad)} clear-margin mismatches"
+        t = ref.iters
+        np.testing.assert_allclose(obj[:t], ref.objective, rtol=OBJ_RTOL, atol=0)
+
+
 def test_batched_rejects_bad_items(skm):
     docs = synth.make_corpus(100, 500, 10, 3, 30, 1.1, 77)
     with pytest.raises(skm.SkmError) as e:

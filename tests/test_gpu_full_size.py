@@ -50,12 +50,12 @@ def _fit(skm, w, dev, n_terms, ids, max_iter, prune=None):
     return a, r, C
 
 
-def _step_locked(skm, w, T, n_sample, n_clusters):
+def _step_locked(skm, w, T, n_sample, n_clusters, prune=None):
     docs = w.corpus()
     ids = w.init_ids()
     dev = _device(docs)
-    _, _, C_prev = _fit(skm, w, dev, docs.n_terms, ids, T - 1)
-    a, r, C = _fit(skm, w, dev, docs.n_terms, ids, T)
+    _, _, C_prev = _fit(skm, w, dev, docs.n_terms, ids, T - 1, prune)
+    a, r, C = _fit(skm, w, dev, docs.n_terms, ids, T, prune)
     assert r.iters == T
     # assignments of sampled documents against the centroids they were scored on
     sample = synth.sample_ids(docs.n_docs, n_sample, 31)
@@ -78,6 +78,13 @@ def _step_locked(skm, w, T, n_sample, n_clusters):
 def test_large_workload_step_locked(skm):
     """N = 2M, d = 250k, k = 10,000, BF16 centroids, NCC, FP64 rescoring."""
     _step_locked(skm, workloads.LARGE, 3, 2000, 40)
+
+
+def test_tweets_workload_with_index_step_locked(skm):
+    """The tweets-like analog at full size (N = 1M, d = 783,304, k = 5000, FP32) with the
+    threshold index of Sec. 3.2 combined with Sec. 3.1 (NCC+INDEX, automatic rules): the
+    sixth step, whose documents the index decides in part, against the oracle."""
+    _step_locked(skm, workloads.TWEETS, 6, 2000, 40, prune="ncc_index")
 
 
 def test_medium_workload_step_locked(skm):

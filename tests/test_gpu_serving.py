@@ -1,9 +1,15 @@
 """Serving form: continuous batching of assignment requests on a resident model while
-clustering jobs run beside it. Every result must equal the same request run alone."""
+clustering jobs run beside it. Every result must equal the same request run alone, and the
+FP64 oracle's result within the method's contract: assignments exact wherever the oracle's
+top-2 margin is at least 1e-5, objectives to 1e-6 relative."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2108_00895_gb300 import synth
+
+MARGIN = 1e-5
+OBJ_RTOL = 1e-6
 
 pytestmark = pytest.mark.gpu
 
@@ -44,6 +50,7 @@ def test_results_alone_equal_results_in_the_mix(env):
         a = int(rng.integers(0, pool.n_docs - n))
         reqs.append(_slice(pool, a, a + n))
     alone = [km.assign(r) for r in reqs]                     # before the server owns the context
+    C_res = km.centroids()                                   # the resident FP32 master
     jobs = [(_slice(pool, 0, 3000), 17), (_slice(pool, 1000, 5000), 40), (_slice(pool, 2000, 4500), 9)]
     job_ids = [synth.init_ids(d.n_docs, k, 100 + q) for q, (d, k) in enumerate(jobs)]
     alone_jobs = []
@@ -60,6 +67,7 @@ def test_results_alone_equal_results_in_the_mix(env):
                 jq = q // 13
                 tickets.append(("f", jq, srv.submit_fit(jobs[jq][0], jobs[jq][1], job_ids[jq], 6)))
         batched = 0
+        served, served_jobs = [], []
         for kind, q, t in tickets:
             res = srv.wait(t)
             assert res["state"] == "done", res["message"]
@@ -67,12 +75,34 @@ def test_results_alone_equal_results_in_the_mix(env):
                 np.testing.assert_array_equal(res["assign"], alone[q][0])
                 np.testing.assert_array_equal(res["score"], alone[q][1])
                 batched += res["batch_docs"] > reqs[q].n_docs
+                served.append((q, res["assign"].copy(), res["score"].copy()))
             else:
                 np.testing.assert_array_equal(res["assign"], alone_jobs[q][0])
                 np.testing.assert_array_equal(res["objective"], alone_jobs[q][1])
+                served_jobs.append((q, res["assign"].copy(), res["objective"].copy()))
         st = srv.stats()
     assert st["assign_done"] == len(reqs) and st["fit_done"] == len(jobs)
     assert st["assign_batches"] < len(reqs) and batched > 0   # requests were merged into batches
+    # against the FP64 oracle: every served assignment on the resident centroids, and every
+    # clustering job run as a plain Lloyd fit from the same initial documents
+    checked = 0
+    for q, a_srv, s_srv in served:
+        a_or, s1, s2 = oracle.assign(reqs[q], C_res)
+        clear = (s1 - s2) >= MARGIN
+        bad = np.nonzero((a_srv != a_or) & clear)[0]
+        assert len(bad) == 0, f"request {q}: {len(bad)} clear-margin mismatches"
+        # the reported score is the BF16-pass (or FP64-rescored) similarity of the winner:
+        # within the BF16 error bound 2^-8 s + FP32 accumulation of the oracle's
+        np.testing.assert_allclose(s_srv, s1, rtol=2.0 ** -7, atol=1e-6)
+        checked += int(clear.sum())
+    assert checked > 0.9 * sum(r.n_docs for r in reqs)
+    for q, a_job, obj_job in served_jobs:
+        d, k = jobs[q]
+        ref = oracle.fit(d, k, job_ids[q], 6)
+        # free-running trajectories agree when no document sits on a near tie
+        assert len(obj_job) == ref.iters
+        np.testing.assert_array_equal(a_job, ref.a)
+        np.testing.assert_allclose(obj_job, ref.objective, rtol=OBJ_RTOL, atol=0)
 
 
 def test_budget_admission_rejects_and_serialises(env):
