@@ -297,7 +297,8 @@ def run_ours(args, w, world, rank, local, dist):
     km = skm.SphericalKMeans(w.k, precision=w.precision, prune=w.prune, max_iter=w.max_iter,
                              shift_tol=w.shift_tol, rescore=args.rescore == "on", tau=args.tau, device=local,
                              stream=stream.cuda_stream, timing=True, sparse_div=args.sparse_div,
-                             index_min_changed=args.index_min_changed, index_max_cands=args.index_max_cands)
+                             index_min_changed=args.index_min_changed, index_max_cands=args.index_max_cands,
+                             head_terms=args.head_terms)
     a_dev = torch.empty(N, dtype=torch.int32, device=dev)
     for _ in range(args.warmup):
         km.fit(d_docs, ids, n_terms=docs.n_terms, assign_out=a_dev)
@@ -314,7 +315,7 @@ def run_ours(args, w, world, rank, local, dist):
     agg = {"fmas": 0, "fmas_exec": 0, "bytes": 0, "ms_score": 0.0, "ms_decide": 0.0, "ms_update": 0.0,
            "launches_total": 0, "launches_score": 0, "sims": 0, "docs_pruned": 0, "docs_full": 0,
            "docs_rescored": 0, "docs_rescored_full": 0, "index_docs": 0, "index_sims": 0, "index_entries": 0,
-           "index_products": 0, "ms_query": 0.0, "ms_index": 0.0}
+           "index_products": 0, "ms_query": 0.0, "ms_index": 0.0, "ms_head": 0.0, "nnz_head": 0}
     objectives = None
     for _ in range(args.steps):
         r = km.fit(d_docs, ids, n_terms=docs.n_terms, assign_out=a_dev)
@@ -322,6 +323,7 @@ def run_ours(args, w, world, rank, local, dist):
         objectives = r.objective
         for key in agg:
             agg[key] += r.stats[key]
+        agg["head_terms"] = r.stats["head_terms"]
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     barrier(dist)
@@ -411,6 +413,7 @@ def run_ours(args, w, world, rank, local, dist):
                                l2="inputs larger than L2 (CSR + centroid matrices >> 129 MB)",
                                objective_last=float(objectives[-1]) if objectives is not None else None,
                                tau=args.tau, rescore=args.rescore, sparse_div=args.sparse_div,
+                               head_terms=agg.get("head_terms"),
                                index_min_changed=args.index_min_changed if w.prune == "ncc_index" else None,
                                index_max_cands=args.index_max_cands if w.prune == "ncc_index" else None),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
@@ -453,7 +456,7 @@ def error_vs_oracle(skm, km, w, docs, ids, d_docs, a_dev, C_fin, objectives, arg
         with skm.SphericalKMeans(w.k, precision=w.precision, prune=w.prune, max_iter=T - 1, shift_tol=w.shift_tol,
                                  rescore=args.rescore == "on", tau=args.tau, device=local, stream=stream.cuda_stream,
                                  sparse_div=args.sparse_div, index_min_changed=args.index_min_changed,
-                                 index_max_cands=args.index_max_cands) as k2:
+                                 index_max_cands=args.index_max_cands, head_terms=args.head_terms) as k2:
             r2 = k2.fit(d_docs, ids, n_terms=docs.n_terms)
             C_prev = k2.centroids() if r2.iters == T - 1 else None
         if C_prev is not None:
@@ -733,6 +736,8 @@ def main():
     ap.add_argument("--rescore", choices=["on", "off"], default="on", help="FP64 rescoring of near ties")
     ap.add_argument("--max-iter", type=int, default=None, help="override the workload's step limit")
     ap.add_argument("--sparse-div", type=int, default=0, help="sparse centroid rows (0 = off)")
+    ap.add_argument("--head-terms", type=int, default=0,
+                    help="BF16: head terms scored on the tensor cores (0 = automatic, -1 = off)")
     ap.add_argument("--case", default=None, help="N,D,K: the workload's recipe at other sizes")
     ap.add_argument("--k", type=int, default=None, help="override the workload's number of clusters")
     args = ap.parse_args()

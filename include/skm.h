@@ -109,11 +109,20 @@ typedef struct {
                                 k >= 1024, and stops for the rest of a fit after a step that
                                 decided fewer than half of the documents through it.
                                 > 0: that cap (at most 256) and none of those rules. */
+    int32_t head_terms;   /* BF16 scoring (k > 256, sparse_div = 0): the products over the
+                             collection's most frequent terms (its head, by document
+                             frequency, fixed for a fit) run on the tensor cores as a dense
+                             matrix product, the other nonzeros on the plain gather path.
+                             0 (the default): automatic, the terms in at least 1/64 of the
+                             documents, at least 64 and at most 1024 of them; > 0: that many
+                             (rounded up to a multiple of 64, at most 2048); -1: off. The
+                             decision stays exact either way (the head's rounding error is
+                             below the BF16 copy's); scores may differ in the last bits. */
 } skm_config;
 
 /* Fills a config with defaults: FP32, no pruning, max_iter 20, shift test off, rescoring
  * on with tau 0, no budget, device 0, default stream, cudaMalloc, sparse rows off, the
- * four index thresholds of Sec. 4.1 with index_min_changed 100. */
+ * four index thresholds of Sec. 4.1 with index_min_changed 100, automatic head terms. */
 SKM_API void skm_config_default(skm_config *cfg, int32_t k);
 
 typedef struct {
@@ -154,6 +163,11 @@ typedef struct {
     int64_t index_products;     /* (term, candidate) products they computed */
     double ms_query;            /* device time in the index query kernel (ms_index also counts
                                    the threshold index builds) */
+    int32_t head_terms;         /* head terms scored on the tensor cores (0: none) */
+    int64_t nnz_head;           /* nonzeros of the scored collection in those terms */
+    double ms_head;             /* device time of the head path outside the scoring kernel:
+                                   head set, split of the collection, head matrices and the
+                                   tensor-core head sums (ms_score then times the tail) */
 } skm_stats;
 
 /* Create a context on cfg->device. cfg is copied. */

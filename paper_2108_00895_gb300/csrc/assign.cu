@@ -27,18 +27,30 @@ __global__ void __launch_bounds__(256) k_score(ScoreArgs a) {
     const int wib = threadIdx.x >> 5;
     const int pos = blockIdx.x * 8 + wib;
     if (pos >= a.n_list) return;
+    const int gpos = a.pos0 + pos;
+    const int n_total = a.n_total > 0 ? a.n_total : a.n_list;
     const int slice = blockIdx.y;
-    const int64_t i = a.doc_list ? (int64_t)a.doc_list[pos] : (int64_t)pos;
+    const int64_t i = a.doc_list ? (int64_t)a.doc_list[gpos] : (int64_t)gpos;
     const int64_t j0 = (int64_t)slice * KS;
     float2 acc[J / 2];
-    slice_accumulate<CT, NV>(a.row_ptr[i], a.row_ptr[i + 1], a.col, a.val,
-                             reinterpret_cast<const CT *>(a.C) + j0 + lane * EPV, a.ldc, stage[wib], lane, acc);
+    const CT *Cs = reinterpret_cast<const CT *>(a.C) + j0 + lane * EPV;
+    if (a.head) {
+        // the tail nonzeros continue the chain from the tensor-core head sums (FP16)
+        const __half2 *hs = reinterpret_cast<const __half2 *>(a.head + (int64_t)pos * a.head_ld + j0 + lane * EPV);
+#pragma unroll
+        for (int u = 0; u < NV; ++u)
+#pragma unroll
+            for (int q = 0; q < EPV / 2; ++q) acc[u * EPV / 2 + q] = __half22float2(hs[u * 16 * EPV + q]);
+        slice_accumulate_add<CT, NV>(a.row_ptr[i], a.row_ptr[i + 1], a.col, a.val, Cs, a.ldc, stage[wib], lane, acc);
+    } else {
+        slice_accumulate<CT, NV>(a.row_ptr[i], a.row_ptr[i + 1], a.col, a.val, Cs, a.ldc, stage[wib], lane, acc);
+    }
     if constexpr (COLLECT) {
-        slice_collect<CT, NV>(acc, j0, lane, a.ncols, a.col_ids, a.thr[pos], a.cand_cnt + pos,
-                              a.cand + (int64_t)pos * a.cap, a.cap);
+        slice_collect<CT, NV>(acc, j0, lane, a.ncols, a.col_ids, a.thr[gpos], a.cand_cnt + gpos,
+                              a.cand + (int64_t)gpos * a.cap, a.cap);
     } else {
         slice_topt_write<CT, NV>(acc, j0, lane, a.ncols, a.col_ids, a.part_s, a.part_j,
-                                 ((int64_t)slice * a.n_list + pos) * TOPT);
+                                 ((int64_t)slice * n_total + gpos) * TOPT);
     }
 }
 
@@ -53,8 +65,10 @@ __global__ void __launch_bounds__(256, 4) k_score_sparse(ScoreArgs a, SparseArgs
     const int wib = threadIdx.x >> 5;
     const int pos = blockIdx.x * 8 + wib;
     if (pos >= a.n_list) return;
+    const int gpos = a.pos0 + pos;
+    const int n_total = a.n_total > 0 ? a.n_total : a.n_list;
     const int slice = blockIdx.y;
-    const int64_t i = a.doc_list ? (int64_t)a.doc_list[pos] : (int64_t)pos;
+    const int64_t i = a.doc_list ? (int64_t)a.doc_list[gpos] : (int64_t)gpos;
     const int64_t j0 = (int64_t)slice * KS;
     const CT *Cs = reinterpret_cast<const CT *>(a.C) + j0 + lane * EPV;
     __shared__ int2 stage[8][32];
@@ -75,11 +89,11 @@ __global__ void __launch_bounds__(256, 4) k_score_sparse(ScoreArgs a, SparseArgs
             atomicAdd(sp.skipped + ((pos + slice) & (SKIP_COUNTERS - 1)), rs.skipped);
     }
     if constexpr (COLLECT) {
-        slice_collect<CT, NV>(acc, j0, lane, a.ncols, a.col_ids, a.thr[pos], a.cand_cnt + pos,
-                              a.cand + (int64_t)pos * a.cap, a.cap);
+        slice_collect<CT, NV>(acc, j0, lane, a.ncols, a.col_ids, a.thr[gpos], a.cand_cnt + gpos,
+                              a.cand + (int64_t)gpos * a.cap, a.cap);
     } else {
         slice_topt_write<CT, NV>(acc, j0, lane, a.ncols, a.col_ids, a.part_s, a.part_j,
-                                 ((int64_t)slice * a.n_list + pos) * TOPT);
+                                 ((int64_t)slice * n_total + gpos) * TOPT);
     }
 }
 
@@ -98,6 +112,7 @@ template <bool COLLECT>
 static cudaError_t launch_score_t(const ScoreArgs &a, int precision, int slice_cols, cudaStream_t st,
                                   const SparseArgs *sp) {
     if (a.n_list <= 0) return cudaSuccess;
+    if (sp && a.head) return cudaErrorInvalidValue;   // sparse rows take no head sums
     const int n_slices = (a.ncols + slice_cols - 1) / slice_cols;
     if (n_slices <= 0) return cudaSuccess;
     dim3 grid((a.n_list + 7) / 8, n_slices);
@@ -155,8 +170,9 @@ cudaError_t launch_collect(const ScoreArgs &a, int precision, int slice_cols, cu
 //   refull   pruned document whose set R may contain unscored centroids: score all k;
 //   full64   R may hold more than TOPT entries: FP64 against all k.
 // rho bounds every score other than s1 (list runner-up, truncated tail, stored bound).
-// tau_i = max(tau, 2 beta s1 / (1 - beta)) makes "accept" exact: any j outside R has
-// exact score below the exact score of the winner.
+// tau_i = max(tau, (2 beta s1 + 2 alpha) / (1 - beta)) makes "accept" exact: any j outside R
+// has exact score below the exact score of the winner (alpha: the absolute error term of a
+// tensor-core head sum, 0 otherwise).
 // ------------------------------------------------------------------------------------
 __global__ void k_decide(DecideArgs a) {
     const int pos = blockIdx.x * blockDim.x + threadIdx.x;
@@ -216,7 +232,11 @@ __global__ void k_decide(DecideArgs a) {
         return;
     }
     const double beta = score_beta(a.precision, nnz);
-    const double tau_i = fmax((double)a.tau, 2.0 * beta * fmax((double)s1, 0.0) / (1.0 - beta));
+    // a tensor-core head sum adds at most 2^-33 sqrt(nnz) + 2^-25 in absolute terms (FP16
+    // subnormals of the operands and of the stored sum)
+    const double alpha = a.head_tc ? ldexp(sqrt((double)nnz), -33) + 5.9604644775390625e-08 : 0.0;
+    const double tau_i =
+        fmax((double)a.tau, (2.0 * beta * fmax((double)s1, 0.0) + 2.0 * alpha) / (1.0 - beta));
     const bool accept = !a.rescore || ((double)s1 - (double)rho > tau_i);
 
     if (accept) {

@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include "score_tc.cuh"
 #include "skm.h"
 #include "skm_host.h"
 #include "skm_kernels.cuh"
@@ -97,8 +98,30 @@ struct skm_ctx {
     // them current (clearing and setting the bits and counts of the entries it rewrites)
     int64_t ti_maint_epoch = -1;
 
+    // tensor-core head of the BF16 scoring pass (score_tc.cu): the head set (chosen by
+    // document frequency when a fit starts, or by the first assignment on loaded centroids),
+    // the staged documents split into head entries and the tail CSR, and the FP16 head
+    // matrices of the full and of the compacted centroid matrix with their TMA maps
+    int32_t tc_h = 0;                 // head terms; 0: the head path is off
+    int32_t tc_d = 0;                 // vocabulary the head set was chosen for
+    int64_t tc_set = 0;               // bumps whenever the head set changes
+    int64_t tc_nnz_head = 0;          // head nonzeros of the current split
+    Buf tc_head_pos, tc_H, tc_df;
+    Buf tc_hcnt, tc_tcnt, tc_hptr, tc_tptr, tc_hent, tc_tcol, tc_tval, tc_scan;
+    int64_t tc_split_docs = -1, tc_split_set = -1;
+    Buf tc_headT, tc_headMT, tc_hs, tc_X;
+    CUtensorMap tc_mapX{};
+    const void *tc_mapX_ptr = nullptr;
+    int32_t tc_mapX_h = 0;
+    int64_t tc_mapX_rows = 0;
+    CUtensorMap tc_mapT{}, tc_mapMT{};
+    const void *tc_mapT_ptr = nullptr, *tc_mapMT_ptr = nullptr;
+    int32_t tc_mapT_h = 0, tc_mapMT_h = 0;
+    int64_t tc_T_epoch = -1, tc_T_set = -1, tc_MT_epoch = -1, tc_MT_set = -1;
+    int32_t tc_MT_cols = -1;
+
     skm_stats stats{};
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_score, ev_decide, ev_update, ev_index, ev_query;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_score, ev_decide, ev_update, ev_index, ev_query, ev_head;
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_next = 0;
 };
@@ -213,6 +236,7 @@ void collect_times(skm_ctx *ctx) {
     ctx->stats.ms_update += sum(ctx->ev_update);
     ctx->stats.ms_index += sum(ctx->ev_index);
     ctx->stats.ms_query += sum(ctx->ev_query);
+    ctx->stats.ms_head += sum(ctx->ev_head);
     ctx->ev_next = 0;
 }
 
@@ -683,6 +707,188 @@ TiQueryArgs ti_args(skm_ctx *ctx, const DevCsr &dc) {
     return q;
 }
 
+// ---------------------------------------------------------------- tensor-core head
+// The head path serves BF16 scoring with 512-column slices and dense rows.
+bool tc_wanted(const skm_ctx *ctx) {
+    return ctx->cfg.precision == SKM_BF16 && ctx->slice == TC_SLICE && ctx->ldc % TC_SLICE == 0 &&
+           ctx->cfg.head_terms >= 0 && ctx->rare_div == 0;
+}
+
+// Head set of the staged collection: the most frequent terms by document frequency (ties
+// to the lower term id), kept in ascending term order so that a document's head entries
+// come in CSR order. Automatic size: the terms in at least 1/64 of the documents, rounded
+// down to a multiple of 64, between 64 and TC_HEAD_AUTO.
+skm_status tc_choose_head(skm_ctx *ctx, const DevCsr &dc) {
+    ctx->tc_h = 0;
+    ctx->tc_d = 0;
+    ctx->tc_set++;
+    if (!tc_wanted(ctx) || dc.d < 64) return SKM_OK;
+    Timed tm(ctx, ctx->ev_head);
+    SKM_TRY(ensure(ctx, ctx->tc_df, sizeof(int32_t) * dc.d));
+    SKM_CUDA(cudaMemsetAsync(ctx->tc_df.p, 0, sizeof(int32_t) * dc.d, ctx->st));
+    SKM_CUDA(launch_term_count(dc.col, dc.nnz, P<int32_t>(ctx->tc_df), ctx->st));
+    std::vector<int32_t> df(dc.d);
+    SKM_CUDA(cudaMemcpyAsync(df.data(), ctx->tc_df.p, sizeof(int32_t) * dc.d, cudaMemcpyDeviceToHost, ctx->st));
+    SKM_TRY(sync(ctx));
+    const int32_t d64 = dc.d / 64 * 64;
+    int32_t h = 0;
+    if (ctx->cfg.head_terms > 0) {
+        h = std::min(TC_HEAD_MAX, (ctx->cfg.head_terms + 63) / 64 * 64);
+    } else {
+        const int64_t min_df = std::max<int64_t>(1, (dc.n + 63) / 64);
+        int64_t cnt = 0;
+        for (int32_t v : df) cnt += v >= min_df;
+        h = (int32_t)std::min<int64_t>(TC_HEAD_AUTO, std::max<int64_t>(64, cnt / 64 * 64));
+    }
+    h = std::min(h, d64);
+    if (h < 64) return SKM_OK;
+    std::vector<int32_t> idx(dc.d);
+    for (int32_t t = 0; t < dc.d; ++t) idx[t] = t;
+    auto more_frequent = [&](int32_t x, int32_t y) { return df[x] > df[y] || (df[x] == df[y] && x < y); };
+    std::nth_element(idx.begin(), idx.begin() + (h - 1), idx.end(), more_frequent);
+    std::vector<int32_t> H(idx.begin(), idx.begin() + h);
+    std::sort(H.begin(), H.end());
+    std::vector<int32_t> pos(dc.d, -1);
+    for (int32_t q = 0; q < h; ++q) pos[H[q]] = q;
+    SKM_TRY(ensure(ctx, ctx->tc_head_pos, sizeof(int32_t) * dc.d));
+    SKM_TRY(ensure(ctx, ctx->tc_H, sizeof(int32_t) * h));
+    SKM_CUDA(cudaMemcpyAsync(ctx->tc_head_pos.p, pos.data(), sizeof(int32_t) * dc.d, cudaMemcpyHostToDevice, ctx->st));
+    SKM_CUDA(cudaMemcpyAsync(ctx->tc_H.p, H.data(), sizeof(int32_t) * h, cudaMemcpyHostToDevice, ctx->st));
+    SKM_TRY(sync(ctx));
+    ctx->tc_h = h;
+    ctx->tc_d = dc.d;
+    return SKM_OK;
+}
+
+// The staged collection split into the head entries and the tail CSR (current head set).
+skm_status tc_split(skm_ctx *ctx, const DevCsr &dc) {
+    if (ctx->tc_h == 0) return SKM_OK;
+    if (ctx->tc_split_docs == ctx->docs_epoch && ctx->tc_split_set == ctx->tc_set) return SKM_OK;
+    Timed tm(ctx, ctx->ev_head);
+    const int64_t n = dc.n;
+    SKM_TRY(ensure(ctx, ctx->tc_hcnt, sizeof(uint32_t) * n));
+    SKM_TRY(ensure(ctx, ctx->tc_tcnt, sizeof(uint32_t) * n));
+    SKM_TRY(ensure(ctx, ctx->tc_hptr, sizeof(int64_t) * (n + 1)));
+    SKM_TRY(ensure(ctx, ctx->tc_tptr, sizeof(int64_t) * (n + 1)));
+    SKM_TRY(ensure(ctx, ctx->tc_scan, ti_scan_scratch(n)));
+    SKM_CUDA(launch_split_count(dc.row_ptr, dc.col, n, P<int32_t>(ctx->tc_head_pos), P<uint32_t>(ctx->tc_hcnt),
+                                P<uint32_t>(ctx->tc_tcnt), ctx->st));
+    SKM_CUDA(launch_ti_scan(P<uint32_t>(ctx->tc_hcnt), n, P<int64_t>(ctx->tc_hptr), P<int64_t>(ctx->tc_scan), ctx->st));
+    SKM_CUDA(launch_ti_scan(P<uint32_t>(ctx->tc_tcnt), n, P<int64_t>(ctx->tc_tptr), P<int64_t>(ctx->tc_scan), ctx->st));
+    int64_t tot[2] = {0, 0};
+    SKM_CUDA(cudaMemcpyAsync(&tot[0], P<int64_t>(ctx->tc_hptr) + n, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->st));
+    SKM_CUDA(cudaMemcpyAsync(&tot[1], P<int64_t>(ctx->tc_tptr) + n, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->st));
+    SKM_TRY(sync(ctx));
+    if (tot[0] + tot[1] != dc.nnz) return fail(ctx, SKM_ERR_CUDA, "head split lost entries");
+    SKM_TRY(ensure(ctx, ctx->tc_hent, sizeof(uint32_t) * std::max<int64_t>(tot[0], 1)));
+    SKM_TRY(ensure(ctx, ctx->tc_tcol, sizeof(int32_t) * std::max<int64_t>(tot[1], 1)));
+    SKM_TRY(ensure(ctx, ctx->tc_tval, sizeof(float) * std::max<int64_t>(tot[1], 1)));
+    SKM_CUDA(launch_split_fill(dc.row_ptr, dc.col, dc.val, n, P<int32_t>(ctx->tc_head_pos), P<int64_t>(ctx->tc_hptr),
+                               P<int64_t>(ctx->tc_tptr), P<uint32_t>(ctx->tc_hent), P<int32_t>(ctx->tc_tcol),
+                               P<float>(ctx->tc_tval), ctx->st));
+    ctx->stats.launches_total += 4;
+    ctx->tc_split_docs = ctx->docs_epoch;
+    ctx->tc_split_set = ctx->tc_set;
+    ctx->tc_nnz_head = tot[0];
+    return SKM_OK;
+}
+
+// FP16 head matrix (2^10 C32 at the head rows, K-major) of the full matrix, or of the
+// compacted matrix of the moved list, current for the resident centroids; its TMA map.
+skm_status tc_matrix(skm_ctx *ctx, bool pruned, int32_t ncols, const CUtensorMap **map) {
+    Buf &B = pruned ? ctx->tc_headMT : ctx->tc_headT;
+    int64_t &epoch = pruned ? ctx->tc_MT_epoch : ctx->tc_T_epoch;
+    int64_t &set = pruned ? ctx->tc_MT_set : ctx->tc_T_set;
+    CUtensorMap &m = pruned ? ctx->tc_mapMT : ctx->tc_mapT;
+    const void *&mp = pruned ? ctx->tc_mapMT_ptr : ctx->tc_mapT_ptr;
+    int32_t &mh = pruned ? ctx->tc_mapMT_h : ctx->tc_mapT_h;
+    const int64_t rows = ctx->ldc;
+    const bool stale = epoch != ctx->cent_epoch || set != ctx->tc_set || (pruned && ctx->tc_MT_cols != ncols);
+    if (stale) {
+        Timed tm(ctx, ctx->ev_head);
+        SKM_TRY(ensure(ctx, B, sizeof(__half) * (size_t)rows * ctx->tc_h));
+        SKM_CUDA(launch_head_matrix(P<float>(ctx->C32), ctx->ldc, P<int32_t>(ctx->tc_H), ctx->tc_h,
+                                    pruned ? P<int32_t>(ctx->moved) : nullptr, ncols, rows, P<__half>(B), ctx->st));
+        ctx->stats.launches_total++;
+        epoch = ctx->cent_epoch;
+        set = ctx->tc_set;
+        if (pruned) ctx->tc_MT_cols = ncols;
+    }
+    if (mp != B.p || mh != ctx->tc_h) {
+        SKM_CUDA(tc_make_map(P<__half>(B), ctx->tc_h, rows, 256, &m));
+        mp = B.p;
+        mh = ctx->tc_h;
+    }
+    *map = &m;
+    return SKM_OK;
+}
+
+bool tc_active(const skm_ctx *ctx) {
+    return ctx->tc_h > 0 && tc_wanted(ctx) && ctx->tc_split_docs == ctx->docs_epoch && ctx->tc_split_set == ctx->tc_set;
+}
+
+// Scoring pass (or collect pass) with the tensor-core head: chunk by chunk of list
+// positions, the head sums of the chunk (k_head_gemm, FP32 in a buffer of at most
+// kHeadSumBytes) and then the scoring kernel over the tail nonzeros, starting from them.
+constexpr int64_t kHeadSumBytes = int64_t(2) << 30;
+
+skm_status tc_score(skm_ctx *ctx, const ScoreArgs &sa0, bool pruned, bool collect) {
+    const CUtensorMap *map = nullptr;
+    SKM_TRY(tc_matrix(ctx, pruned, sa0.ncols, &map));
+    const int64_t ld = ctx->ldc;
+    const int32_t n_slices = (sa0.ncols + TC_SLICE - 1) / TC_SLICE;
+    int64_t cap_bytes = kHeadSumBytes;
+    if (ctx->cfg.mem_budget) cap_bytes = std::min<int64_t>(cap_bytes, (int64_t)(ctx->cfg.mem_budget / 16));
+    int64_t chunk = cap_bytes / (int64_t)(sizeof(__half) * ld) / 256 * 256;
+    chunk = std::max<int64_t>(256, std::min<int64_t>(chunk, ((int64_t)sa0.n_list + 255) / 256 * 256));
+    SKM_TRY(ensure(ctx, ctx->tc_hs, sizeof(__half) * (size_t)chunk * (size_t)ld));
+    // dense head rows of a chunk's documents (the GEMM's document operand) and their TMA map
+    SKM_TRY(ensure(ctx, ctx->tc_X, sizeof(__half) * (size_t)chunk * (size_t)ctx->tc_h));
+    if (ctx->tc_mapX_ptr != ctx->tc_X.p || ctx->tc_mapX_h != ctx->tc_h || ctx->tc_mapX_rows != chunk) {
+        SKM_CUDA(tc_make_map(P<__half>(ctx->tc_X), ctx->tc_h, chunk, 128, &ctx->tc_mapX));
+        ctx->tc_mapX_ptr = ctx->tc_X.p;
+        ctx->tc_mapX_h = ctx->tc_h;
+        ctx->tc_mapX_rows = chunk;
+    }
+    for (int64_t p0 = 0; p0 < sa0.n_list; p0 += chunk) {
+        const int32_t n = (int32_t)std::min<int64_t>(chunk, sa0.n_list - p0);
+        HeadGemmArgs g{};
+        g.hptr = P<int64_t>(ctx->tc_hptr);
+        g.hent = P<uint32_t>(ctx->tc_hent);
+        g.doc_list = sa0.doc_list;
+        g.pos0 = (int32_t)p0;
+        g.n = n;
+        g.h = ctx->tc_h;
+        g.n_cblk = 2 * n_slices;
+        g.out = P<__half>(ctx->tc_hs);
+        g.ld = ld;
+        g.err = P<int32_t>(ctx->counters) + CNT_ERR;
+        {
+            Timed tm(ctx, ctx->ev_head);
+            const int32_t rows = (int32_t)std::min<int64_t>(chunk, ((int64_t)n + 255) / 256 * 256);
+            SKM_CUDA(launch_head_rows(g, rows, P<__half>(ctx->tc_X), ctx->st));
+            SKM_CUDA(launch_head_gemm(g, ctx->tc_mapX, *map, ctx->st));
+        }
+        ScoreArgs sa = sa0;
+        sa.row_ptr = P<int64_t>(ctx->tc_tptr);
+        sa.col = P<int32_t>(ctx->tc_tcol);
+        sa.val = P<float>(ctx->tc_tval);
+        sa.pos0 = (int32_t)p0;
+        sa.n_list = n;
+        sa.n_total = sa0.n_list;
+        sa.head = P<__half>(ctx->tc_hs);
+        sa.head_ld = ld;
+        if (collect) {
+            SKM_CUDA(launch_collect(sa, SKM_BF16, ctx->slice, ctx->st));
+        } else {
+            Timed tm(ctx, ctx->ev_score);
+            SKM_CUDA(launch_score(sa, SKM_BF16, ctx->slice, ctx->st));
+        }
+        ctx->stats.launches_total += 3;
+    }
+    return SKM_OK;
+}
+
 skm_status score_and_decide(skm_ctx *ctx, const DevCsr &dc, const int32_t *list, int32_t n_list,
                             bool pruned, int32_t n_moved, const int32_t *a_old, int32_t *a_new,
                             float *score_out) {
@@ -708,11 +914,14 @@ skm_status score_and_decide(skm_ctx *ctx, const DevCsr &dc, const int32_t *list,
     sa.part_s = P<float>(ctx->part_s);
     sa.part_j = P<int32_t>(ctx->part_j);
     const int n_slices = (sa.ncols + ctx->slice - 1) / ctx->slice;
-    RareView rv;
-    SparseArgs spa{};
-    SKM_TRY(ensure_rare(ctx, dc, pruned, sa.ncols, rv));
-    const SparseArgs *sp = apply_rare(ctx, rv, sa, spa);
-    {
+    const bool tc = prec == SKM_BF16 && tc_active(ctx);
+    if (tc) {
+        SKM_TRY(tc_score(ctx, sa, pruned, false));
+    } else {
+        RareView rv;
+        SparseArgs spa{};
+        SKM_TRY(ensure_rare(ctx, dc, pruned, sa.ncols, rv));
+        const SparseArgs *sp = apply_rare(ctx, rv, sa, spa);
         Timed tm(ctx, ctx->ev_score);
         SKM_CUDA(launch_score(sa, prec, ctx->slice, ctx->st, sp));
     }
@@ -727,6 +936,7 @@ skm_status score_and_decide(skm_ctx *ctx, const DevCsr &dc, const int32_t *list,
     da.part_j = sa.part_j;
     da.row_ptr = dc.row_ptr;
     da.precision = prec;
+    da.head_tc = tc ? 1 : 0;
     da.tau = (float)ctx->cfg.rescore_tau;
     da.rescore = ctx->cfg.rescore;
     da.pruned = pruned ? 1 : 0;
@@ -754,8 +964,16 @@ skm_status score_and_decide(skm_ctx *ctx, const DevCsr &dc, const int32_t *list,
 
 // Sum of nonzeros of listed documents (host copy of row_ptr needed): approximated on the
 // device side is not needed for correctness; the counters below use the list sizes.
+// A bounded wait of the tensor-core scoring kernel gave up (bit 32 of the error counter).
+skm_status check_tc_timeout(skm_ctx *ctx) {
+    if (ctx->h_counters[CNT_ERR] & 32)
+        return fail(ctx, SKM_ERR_TIMEOUT, "a bounded wait of the tensor-core scoring kernel gave up");
+    return SKM_OK;
+}
+
 skm_status rescore_queues(skm_ctx *ctx, const DevCsr &dc, int32_t *a_new, float *score_out) {
     SKM_TRY(read_counters(ctx));
+    SKM_TRY(check_tc_timeout(ctx));
     const int n_rs = ctx->h_counters[CNT_RESCORE];
     const int n_col = ctx->h_counters[CNT_COLLECT];
     RescoreArgs ra{};
@@ -797,11 +1015,16 @@ skm_status rescore_queues(skm_ctx *ctx, const DevCsr &dc, int32_t *a_new, float 
         sa.cand_cnt = P<int32_t>(ctx->cand_cnt);
         sa.cand = P<int32_t>(ctx->cand);
         sa.cap = kCollectCap;
-        RareView rv;
-        SparseArgs spa{};
-        SKM_TRY(ensure_rare(ctx, dc, false, ctx->cfg.k, rv));
-        const SparseArgs *sp = apply_rare(ctx, rv, sa, spa);
-        SKM_CUDA(launch_collect(sa, ctx->cfg.precision, ctx->slice, ctx->st, sp));
+        if (ctx->cfg.precision == SKM_BF16 && tc_active(ctx)) {
+            // the collect pass recomputes the scoring pass's scores: the same head path
+            SKM_TRY(tc_score(ctx, sa, false, true));
+        } else {
+            RareView rv;
+            SparseArgs spa{};
+            SKM_TRY(ensure_rare(ctx, dc, false, ctx->cfg.k, rv));
+            const SparseArgs *sp = apply_rare(ctx, rv, sa, spa);
+            SKM_CUDA(launch_collect(sa, ctx->cfg.precision, ctx->slice, ctx->st, sp));
+        }
         ra.count = nullptr;
         ra.n_fixed = nb;
         ra.rs_doc = sa.doc_list;
@@ -814,6 +1037,7 @@ skm_status rescore_queues(skm_ctx *ctx, const DevCsr &dc, int32_t *a_new, float 
     int n_f64 = 0;
     if (n_col > 0) {
         SKM_TRY(read_counters(ctx));
+        SKM_TRY(check_tc_timeout(ctx));
         n_f64 = ctx->h_counters[CNT_FULL64];
     }
     if (n_f64 > 0) {
@@ -1043,7 +1267,7 @@ skm_status skm_create(const skm_config *cfg, skm_ctx **out) {
     *out = nullptr;
     if (cfg->k < 1 || cfg->max_iter < 1 || (cfg->precision != SKM_FP32 && cfg->precision != SKM_BF16) ||
         (cfg->prune != SKM_PRUNE_NONE && cfg->prune != SKM_PRUNE_NCC && cfg->prune != SKM_PRUNE_NCC_INDEX) ||
-        cfg->index_max_cands < 0 ||
+        cfg->index_max_cands < 0 || cfg->head_terms < -1 ||
         !(cfg->rescore_tau >= 0.0) || (cfg->alloc == nullptr) != (cfg->free == nullptr) || cfg->sparse_div < 0)
         return SKM_ERR_INVALID;
     if (cfg->prune == SKM_PRUNE_NCC_INDEX) {
@@ -1246,6 +1470,10 @@ skm_status skm_fit(skm_ctx *ctx, const skm_csr *docs, const int32_t *init_doc_id
     SKM_TRY(ensure(ctx, ctx->init_ids, sizeof(int32_t) * k));
     Postings pg;
     SKM_TRY(build_postings(ctx, dc, pg));
+    // the head set of the tensor-core scoring path is fixed for the fit (scores stay a pure
+    // function of the document and the centroid across its passes)
+    SKM_TRY(tc_choose_head(ctx, dc));
+    SKM_TRY(tc_split(ctx, dc));
     SKM_CUDA(cudaMemcpyAsync(ctx->init_ids.p, init_doc_ids, sizeof(int32_t) * k, cudaMemcpyHostToDevice, ctx->st));
     SKM_CUDA(launch_init_centroids(dc.row_ptr, dc.col, dc.val, P<int32_t>(ctx->init_ids), k, P<float>(ctx->C32),
                                    ctx->cfg.precision == SKM_BF16 ? P<__nv_bfloat16>(ctx->C16) : nullptr,
@@ -1385,6 +1613,8 @@ skm_status skm_fit(skm_ctx *ctx, const skm_csr *docs, const int32_t *init_doc_id
     SKM_TRY(sync(ctx));
     collect_times(ctx);
     ctx->stats.iters = it;
+    ctx->stats.head_terms = tc_active(ctx) ? ctx->tc_h : 0;
+    ctx->stats.nnz_head = tc_active(ctx) ? ctx->tc_nnz_head : 0;
     if (use_index) {
         unsigned long long h[4];
         SKM_CUDA(cudaMemcpyAsync(h, ctx->ti_stats.p, sizeof h, cudaMemcpyDeviceToHost, ctx->st));
@@ -1417,6 +1647,12 @@ skm_status skm_assign(skm_ctx *ctx, const skm_csr *docs, int32_t *assign_out, fl
     SKM_TRY(stage_docs(ctx, docs, dc));
     const int64_t N = dc.n;
     SKM_TRY(ensure_doc_bufs(ctx, N));
+    // the head set of the last fit (or of the first assignment on loaded centroids) is kept,
+    // so that repeated assignments score every document the same way
+    if (ctx->tc_h == 0 || ctx->tc_d != dc.d) {
+        if (tc_wanted(ctx)) SKM_TRY(tc_choose_head(ctx, dc));
+    }
+    SKM_TRY(tc_split(ctx, dc));
     int32_t *a_new = P<int32_t>(ctx->abuf[0]);
     SKM_TRY(reset_counters(ctx));
     SKM_TRY(reset_skipped(ctx));
@@ -1450,6 +1686,8 @@ skm_status skm_assign(skm_ctx *ctx, const skm_csr *docs, int32_t *assign_out, fl
     ctx->stats.bytes = 8 * dc.nnz + 20 * N +
                        (int64_t)ctx->d * ctx->cfg.k * (ctx->cfg.precision == SKM_BF16 ? 2 : 4);
     ctx->stats.iters = 1;
+    ctx->stats.head_terms = tc_active(ctx) ? ctx->tc_h : 0;
+    ctx->stats.nnz_head = tc_active(ctx) ? ctx->tc_nnz_head : 0;
     if (s == SKM_OK) {
         int64_t sk = 0;
         s = read_skipped(ctx, &sk);

@@ -158,19 +158,16 @@ __device__ __forceinline__ void sparse_rows(int q0, int q1, RareSlice &rs, int l
     __syncwarp();
 }
 
-// Scoring of one document against one slice: acc (lane's J columns, as pairs) = sum over
-// the nonzeros t in [beg, end), in CSR order, of x_t * C[t, lane columns] with one fused
-// multiply-add per column. Cs points at the lane's first column of row 0; stage holds the
-// warp's 32 staged (t, x) pairs. Rows of G nonzeros are loaded together.
+// acc (lane's J columns, as pairs) += x_t * C[t, lane columns] for the nonzeros t in
+// [beg, end), in CSR order, one fused multiply-add per column and nonzero. Cs points at the
+// lane's first column of row 0; stage holds the warp's 32 staged (t, x) pairs. Rows of G
+// nonzeros are loaded together.
 template <typename CT, int NV>
-__device__ __forceinline__ void slice_accumulate(int64_t beg, int64_t end, const int32_t *col, const float *val,
-                                                 const CT *Cs, int64_t ldc, int2 *stage, int lane,
-                                                 float2 (&acc)[NV * 16 / (int)sizeof(CT) / 2]) {
+__device__ __forceinline__ void slice_accumulate_add(int64_t beg, int64_t end, const int32_t *col, const float *val,
+                                                     const CT *Cs, int64_t ldc, int2 *stage, int lane,
+                                                     float2 (&acc)[NV * 16 / (int)sizeof(CT) / 2]) {
     constexpr int EPV = 16 / (int)sizeof(CT);
-    constexpr int J = NV * EPV;
     constexpr int G = NV >= 4 ? 2 : 4;
-#pragma unroll
-    for (int q = 0; q < J / 2; ++q) acc[q] = make_float2(0.f, 0.f);
     for (int64_t b = beg; b < end; b += 32) {
         const int n = (int)min((int64_t)32, end - b);
         __syncwarp();
@@ -200,6 +197,18 @@ __device__ __forceinline__ void slice_accumulate(int64_t beg, int64_t end, const
             fma_row<CT, NV>(acc, __int_as_float(tv.y), w);
         }
     }
+}
+
+// Scoring of one document against one slice: acc = sum over the nonzeros in [beg, end), in
+// CSR order, of x_t * C[t, lane columns] (slice_accumulate_add from zero).
+template <typename CT, int NV>
+__device__ __forceinline__ void slice_accumulate(int64_t beg, int64_t end, const int32_t *col, const float *val,
+                                                 const CT *Cs, int64_t ldc, int2 *stage, int lane,
+                                                 float2 (&acc)[NV * 16 / (int)sizeof(CT) / 2]) {
+    constexpr int J = NV * 16 / (int)sizeof(CT);
+#pragma unroll
+    for (int q = 0; q < J / 2; ++q) acc[q] = make_float2(0.f, 0.f);
+    slice_accumulate_add<CT, NV>(beg, end, col, val, Cs, ldc, stage, lane, acc);
 }
 
 // slice_accumulate with sparse rows: negative column entries ~t mark rows stored by their
@@ -314,7 +323,11 @@ __device__ __forceinline__ void slice_collect(const float2 (&acc)[NV * 16 / (int
 // u_c the unit roundoff of the centroid copy (0 for the FP32 master itself; 2^-8 for BF16
 // round-to-nearest-even: an 8-bit significand, so a value just above a power of two can
 // move by half of a 2^-7 spacing) and gamma_n = n u / (1 - n u), u = 2^-24, n = nonzeros
-// of the document (one rounding per fused multiply-add).
+// of the document (one rounding per fused multiply-add). With a tensor-core head sum (BF16
+// only) the head part's relative error, 2^-10 + 2^-11 + 2^-22 + (h / 16 + 2) 2^-22 at most
+// (FP16 operands, FP16 stored sum, FP32 accumulation), is below u_c, and the sum enters the
+// chain as one more term, which the head's own nonzeros outnumber: the same beta holds, plus
+// the absolute term that the decision adds.
 // ------------------------------------------------------------------------------------
 __device__ __forceinline__ double score_beta(int precision, int64_t nnz) {
     const double u = 5.9604644775390625e-08;  // 2^-24

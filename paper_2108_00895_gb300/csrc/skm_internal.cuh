@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -101,6 +102,15 @@ struct ScoreArgs {
     int32_t *cand_cnt;
     int32_t *cand;
     int32_t cap;
+    // a launch over the list positions [pos0, pos0 + n_list) of a list of n_total positions:
+    // doc_list, part, thr, cand_cnt and cand are indexed by the list position (pos0 = 0 and
+    // n_total = 0, read as n_list, for the whole list)
+    int32_t pos0;
+    int32_t n_total;
+    // nullable: head sums (tensor-core part of the score, FP16); the accumulators of list
+    // position p start from head[(p - pos0) * head_ld + column] instead of zero
+    const __half *head;
+    int64_t head_ld;
 };
 
 // Sparse rows of the scored matrix (see rare.cu): the column stream passed in ScoreArgs.col

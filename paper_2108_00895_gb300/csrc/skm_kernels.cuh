@@ -30,6 +30,7 @@ struct DecideArgs {
     const int32_t *part_j;
     const int64_t *row_ptr;
     int precision;             // 0 FP32, 1 BF16 (error bound of the scored copy)
+    int head_tc;               // 1: scores include a tensor-core head sum (absolute error term)
     float tau;
     int rescore;
     int pruned;                // 1: documents of the pruned class (fold in stored state)

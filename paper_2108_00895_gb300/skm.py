@@ -44,7 +44,7 @@ class skm_config(ctypes.Structure):
                 ("alloc_user", ctypes.c_void_p), ("timing", ctypes.c_int32),
                 ("sparse_div", ctypes.c_int32), ("index_levels", ctypes.c_int32),
                 ("index_lambda", ctypes.c_double * 4), ("index_min_changed", ctypes.c_int32),
-                ("index_max_cands", ctypes.c_int32)]
+                ("index_max_cands", ctypes.c_int32), ("head_terms", ctypes.c_int32)]
 
 
 class skm_csr(ctypes.Structure):
@@ -64,7 +64,8 @@ class skm_stats(ctypes.Structure):
                 ("ms_index", ctypes.c_double), ("sparse_rows", ctypes.c_int64),
                 ("sparse_entries", ctypes.c_int64), ("index_docs", ctypes.c_int64),
                 ("index_sims", ctypes.c_int64), ("index_entries", ctypes.c_int64),
-                ("index_products", ctypes.c_int64), ("ms_query", ctypes.c_double)]
+                ("index_products", ctypes.c_int64), ("ms_query", ctypes.c_double),
+                ("head_terms", ctypes.c_int32), ("nnz_head", ctypes.c_int64), ("ms_head", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -398,14 +399,16 @@ class SphericalKMeans:
     changed; -1 = every step; documents with more than index_max_cands candidates, 0 =
     automatic, are scored densely); rescore: FP64 rescoring of near ties; tau: margin threshold;
     sparse_div: centroid rows with at most k / sparse_div nonzeros are scored from their
-    nonzero lists (0 = off; results are identical either way).
+    nonzero lists (0 = off; results are identical either way). head_terms: BF16 scoring of
+    the collection's most frequent terms on the tensor cores (0 = automatic, -1 = off, > 0 =
+    that many; assignments are exact either way).
     """
 
     def __init__(self, k: int, precision: str = "fp32", prune: str = "none", max_iter: int = 20,
                  shift_tol: float = -1.0, rescore: bool = True, tau: float = 0.0, device: int = 0,
                  stream: int | None = None, mem_budget: int = 0, timing: bool = False,
                  allocator: str = "torch", sparse_div: int = 0, index_lambdas=None,
-                 index_min_changed: int | None = None, index_max_cands: int = 0):
+                 index_min_changed: int | None = None, index_max_cands: int = 0, head_terms: int = 0):
         self.lib = load()
         cfg = skm_config_default(k)
         cfg.precision = {"fp32": SKM_FP32, "bf16": SKM_BF16}[precision]
@@ -428,6 +431,7 @@ class SphericalKMeans:
         cfg.device = int(device)
         cfg.timing = int(bool(timing))
         cfg.sparse_div = int(sparse_div)
+        cfg.head_terms = int(head_terms)
         if stream is None and allocator == "torch":
             import torch
             stream = torch.cuda.current_stream(device).cuda_stream

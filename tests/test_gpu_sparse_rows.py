@@ -33,7 +33,10 @@ def _trained(docs, k, seed, iters=2):
 
 
 def _assign(skm, C, docs, precision, div, rescore=True):
-    with skm.SphericalKMeans(C.shape[1], precision=precision, sparse_div=div, rescore=rescore) as km:
+    # sparse rows replace the dense rows of the plain scoring pass, which is what they are
+    # compared with: the tensor-core head path (another rounding of the frequent terms) is off
+    with skm.SphericalKMeans(C.shape[1], precision=precision, sparse_div=div, rescore=rescore,
+                             head_terms=-1) as km:
         km.set_centroids(C)
         a, s = km.assign(docs)
         st = km.stats()
@@ -84,7 +87,8 @@ def test_fit_with_sparse_rows_bit_identical(skm, precision):
     ids = w.init_ids()
     runs = {}
     for div in (0, 8, 1):
-        with skm.SphericalKMeans(w.k, precision=precision, prune="ncc", max_iter=12, sparse_div=div) as km:
+        with skm.SphericalKMeans(w.k, precision=precision, prune="ncc", max_iter=12, sparse_div=div,
+                                 head_terms=-1) as km:
             r = km.fit(docs, ids)
             runs[div] = (r, km.centroids())
     r0, C0 = runs[0]
