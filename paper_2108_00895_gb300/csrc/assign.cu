@@ -74,6 +74,14 @@ __global__ void __launch_bounds__(256, 4) k_score_sparse(ScoreArgs a, SparseArgs
     __shared__ int2 stage[8][32];
     extern __shared__ float4 scratch4[];
     float2 acc[J / 2];
+    if (a.head) {
+        // the tail nonzeros continue the chain from the tensor-core head sums (FP16)
+        const __half2 *hs = reinterpret_cast<const __half2 *>(a.head + (int64_t)pos * a.head_ld + j0 + lane * EPV);
+#pragma unroll
+        for (int u = 0; u < NV; ++u)
+#pragma unroll
+            for (int q = 0; q < EPV / 2; ++q) acc[u * EPV / 2 + q] = __half22float2(hs[u * 16 * EPV + q]);
+    }
     {
         RareSlice rs;
         rs.ptr = sp.ptr;
@@ -84,7 +92,7 @@ __global__ void __launch_bounds__(256, 4) k_score_sparse(ScoreArgs a, SparseArgs
         rs.sacc = reinterpret_cast<float *>(scratch4) + wib * (KS + RARE_SPARE);
         rs.stg = reinterpret_cast<char *>(scratch4) + sizeof(float) * 8 * (KS + RARE_SPARE) + wib * RARE_STAGE_BYTES;
         slice_accumulate_sparse<CT, NV>(a.row_ptr[i], a.row_ptr[i + 1], a.col, a.val, Cs, a.ldc, stage[wib], lane,
-                                        acc, rs);
+                                        acc, rs, a.head == nullptr);
         if (sp.skipped && rs.skipped && lane == 0)
             atomicAdd(sp.skipped + ((pos + slice) & (SKIP_COUNTERS - 1)), rs.skipped);
     }
@@ -112,7 +120,6 @@ template <bool COLLECT>
 static cudaError_t launch_score_t(const ScoreArgs &a, int precision, int slice_cols, cudaStream_t st,
                                   const SparseArgs *sp) {
     if (a.n_list <= 0) return cudaSuccess;
-    if (sp && a.head) return cudaErrorInvalidValue;   // sparse rows take no head sums
     const int n_slices = (a.ncols + slice_cols - 1) / slice_cols;
     if (n_slices <= 0) return cudaSuccess;
     dim3 grid((a.n_list + 7) / 8, n_slices);

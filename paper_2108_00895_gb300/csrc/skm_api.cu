@@ -109,7 +109,8 @@ struct skm_ctx {
     Buf tc_head_pos, tc_H, tc_df;
     Buf tc_hcnt, tc_tcnt, tc_hptr, tc_tptr, tc_hent, tc_tcol, tc_tval, tc_scan;
     int64_t tc_split_docs = -1, tc_split_set = -1;
-    Buf tc_headT, tc_headMT, tc_hs, tc_X;
+    Buf tc_headT, tc_headMT, tc_hs, tc_X, tc_tcolm;
+    int64_t tc_colm_epoch = -1, tc_colm_split = -1, tc_colm_set = -1;
     CUtensorMap tc_mapX{};
     const void *tc_mapX_ptr = nullptr;
     int32_t tc_mapX_h = 0;
@@ -593,12 +594,13 @@ skm_status build_c_index(skm_ctx *ctx) {
     return SKM_OK;
 }
 
-skm_status ensure_rare(skm_ctx *ctx, const DevCsr &dc, bool pruned, int32_t ncols, RareView &rv) {
+skm_status ensure_rare(skm_ctx *ctx, const DevCsr &dc, bool pruned, int32_t ncols, RareView &rv,
+                       bool mark_collection = true) {
     rv = RareView{};
     if (ctx->rare_div <= 0) return SKM_OK;
     Timed tm(ctx, ctx->ev_index);
     SKM_TRY(build_c_index(ctx));
-    if (ctx->colm_epoch != ctx->rare_c_epoch || ctx->colm_docs != ctx->docs_epoch) {
+    if (mark_collection && (ctx->colm_epoch != ctx->rare_c_epoch || ctx->colm_docs != ctx->docs_epoch)) {
         SKM_TRY(ensure(ctx, ctx->colm, sizeof(int32_t) * (size_t)dc.nnz));
         SKM_CUDA(launch_mark_rare(dc.col, dc.nnz, P<uint8_t>(ctx->rflag), P<int32_t>(ctx->colm), ctx->st));
         ctx->stats.launches_total++;
@@ -711,7 +713,7 @@ TiQueryArgs ti_args(skm_ctx *ctx, const DevCsr &dc) {
 // The head path serves BF16 scoring with 512-column slices and dense rows.
 bool tc_wanted(const skm_ctx *ctx) {
     return ctx->cfg.precision == SKM_BF16 && ctx->slice == TC_SLICE && ctx->ldc % TC_SLICE == 0 &&
-           ctx->cfg.head_terms >= 0 && ctx->rare_div == 0;
+           ctx->cfg.head_terms >= 0;
 }
 
 // Head set of the staged collection: the most frequent terms by document frequency (ties
@@ -832,9 +834,33 @@ bool tc_active(const skm_ctx *ctx) {
 // kHeadSumBytes) and then the scoring kernel over the tail nonzeros, starting from them.
 constexpr int64_t kHeadSumBytes = int64_t(2) << 30;
 
-skm_status tc_score(skm_ctx *ctx, const ScoreArgs &sa0, bool pruned, bool collect) {
+skm_status tc_score(skm_ctx *ctx, const DevCsr &dc, const ScoreArgs &sa0, bool pruned, bool collect) {
     const CUtensorMap *map = nullptr;
     SKM_TRY(tc_matrix(ctx, pruned, sa0.ncols, &map));
+    // sparse centroid rows (section 6a) over the tail: the tail's column stream marked the
+    // same way as the full collection's
+    RareView rv;
+    SKM_TRY(ensure_rare(ctx, dc, pruned, sa0.ncols, rv, false));
+    SparseArgs spa{};
+    const SparseArgs *sp = nullptr;
+    if (rv.ptr) {
+        const int64_t n_tail = dc.nnz - ctx->tc_nnz_head;
+        if (ctx->tc_colm_epoch != ctx->rare_c_epoch || ctx->tc_colm_split != ctx->tc_split_docs ||
+            ctx->tc_colm_set != ctx->tc_set) {
+            SKM_TRY(ensure(ctx, ctx->tc_tcolm, sizeof(int32_t) * (size_t)std::max<int64_t>(n_tail, 1)));
+            SKM_CUDA(launch_mark_rare(P<int32_t>(ctx->tc_tcol), n_tail, P<uint8_t>(ctx->rflag),
+                                      P<int32_t>(ctx->tc_tcolm), ctx->st));
+            ctx->stats.launches_total++;
+            ctx->tc_colm_epoch = ctx->rare_c_epoch;
+            ctx->tc_colm_split = ctx->tc_split_docs;
+            ctx->tc_colm_set = ctx->tc_set;
+        }
+        spa.ptr = rv.ptr;
+        spa.ent = rv.ent;
+        spa.n_slices = rv.n_slices;
+        spa.skipped = ctx->skipped.p ? P<unsigned long long>(ctx->skipped) : nullptr;
+        sp = &spa;
+    }
     const int64_t ld = ctx->ldc;
     const int32_t n_slices = (sa0.ncols + TC_SLICE - 1) / TC_SLICE;
     int64_t cap_bytes = kHeadSumBytes;
@@ -871,7 +897,7 @@ skm_status tc_score(skm_ctx *ctx, const ScoreArgs &sa0, bool pruned, bool collec
         }
         ScoreArgs sa = sa0;
         sa.row_ptr = P<int64_t>(ctx->tc_tptr);
-        sa.col = P<int32_t>(ctx->tc_tcol);
+        sa.col = sp ? P<int32_t>(ctx->tc_tcolm) : P<int32_t>(ctx->tc_tcol);
         sa.val = P<float>(ctx->tc_tval);
         sa.pos0 = (int32_t)p0;
         sa.n_list = n;
@@ -879,10 +905,10 @@ skm_status tc_score(skm_ctx *ctx, const ScoreArgs &sa0, bool pruned, bool collec
         sa.head = P<__half>(ctx->tc_hs);
         sa.head_ld = ld;
         if (collect) {
-            SKM_CUDA(launch_collect(sa, SKM_BF16, ctx->slice, ctx->st));
+            SKM_CUDA(launch_collect(sa, SKM_BF16, ctx->slice, ctx->st, sp));
         } else {
             Timed tm(ctx, ctx->ev_score);
-            SKM_CUDA(launch_score(sa, SKM_BF16, ctx->slice, ctx->st));
+            SKM_CUDA(launch_score(sa, SKM_BF16, ctx->slice, ctx->st, sp));
         }
         ctx->stats.launches_total += 3;
     }
@@ -916,7 +942,7 @@ skm_status score_and_decide(skm_ctx *ctx, const DevCsr &dc, const int32_t *list,
     const int n_slices = (sa.ncols + ctx->slice - 1) / ctx->slice;
     const bool tc = prec == SKM_BF16 && tc_active(ctx);
     if (tc) {
-        SKM_TRY(tc_score(ctx, sa, pruned, false));
+        SKM_TRY(tc_score(ctx, dc, sa, pruned, false));
     } else {
         RareView rv;
         SparseArgs spa{};
@@ -1017,7 +1043,7 @@ skm_status rescore_queues(skm_ctx *ctx, const DevCsr &dc, int32_t *a_new, float 
         sa.cap = kCollectCap;
         if (ctx->cfg.precision == SKM_BF16 && tc_active(ctx)) {
             // the collect pass recomputes the scoring pass's scores: the same head path
-            SKM_TRY(tc_score(ctx, sa, false, true));
+            SKM_TRY(tc_score(ctx, dc, sa, false, true));
         } else {
             RareView rv;
             SparseArgs spa{};

@@ -213,16 +213,18 @@ __device__ __forceinline__ void slice_accumulate(int64_t beg, int64_t end, const
 
 // slice_accumulate with sparse rows: negative column entries ~t mark rows stored by their
 // nonzeros (see RareSlice); runs of dense and sparse rows alternate in CSR order, so every
-// score is the one slice_accumulate computes from the dense matrix, bit for bit.
+// score is the one slice_accumulate computes from the dense matrix, bit for bit. With
+// from_zero = false the chain continues from the given accumulators (head sums).
 template <typename CT, int NV>
 __device__ __forceinline__ void slice_accumulate_sparse(int64_t beg, int64_t end, const int32_t *col,
                                                         const float *val, const CT *Cs, int64_t ldc, int2 *stage,
                                                         int lane, float2 (&acc)[NV * 16 / (int)sizeof(CT) / 2],
-                                                        RareSlice &rs) {
+                                                        RareSlice &rs, bool from_zero = true) {
     constexpr int EPV = 16 / (int)sizeof(CT);
     constexpr int J = NV * EPV;
+    if (from_zero)
 #pragma unroll
-    for (int q = 0; q < J / 2; ++q) acc[q] = make_float2(0.f, 0.f);
+        for (int q = 0; q < J / 2; ++q) acc[q] = make_float2(0.f, 0.f);
     for (int64_t b = beg; b < end; b += 32) {
         const int n = (int)min((int64_t)32, end - b);
         __syncwarp();

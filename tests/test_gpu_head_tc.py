@@ -169,3 +169,30 @@ def test_head_path_off_below_its_shapes(skm):
             km.set_centroids(C)
             km.assign(dd)
             assert km.stats()["head_terms"] == 0
+
+
+@pytest.mark.parametrize("div", [8, 1])
+def test_sparse_rows_on_the_tail_bit_identical(skm, div):
+    """Sparse centroid rows (lists of a row's nonzeros) over the tail nonzeros: only products
+    with exact zeros are skipped, so the scores equal those of the dense rows bit for bit, on
+    the assignment step and over a whole NCC fit."""
+    docs = synth.make_corpus(3000, 20000, 80, 5, 600, 1.05, 911)
+    k = 700
+    C = oracle.fit(docs, k, synth.init_ids(docs.n_docs, k, 912), 2).C.astype(np.float32)
+    a0, s0, st0 = _assign(skm, docs, C, k, 128)
+    a1, s1, st1 = _assign(skm, docs, C, k, 128, sparse_div=div)
+    assert st1["head_terms"] == 128 and st1["sparse_rows"] > 0
+    np.testing.assert_array_equal(a1, a0)
+    np.testing.assert_array_equal(s1.view(np.uint32), s0.view(np.uint32))
+    ids = synth.init_ids(docs.n_docs, k, 913)
+    out = {}
+    for sd in (0, div):
+        with skm.SphericalKMeans(k, precision="bf16", prune="ncc", max_iter=8, head_terms=128, sparse_div=sd) as km:
+            r = km.fit(docs, ids)
+            out[sd] = (r, km.centroids())
+    (r0, C0), (r1, C1) = out[0], out[div]
+    assert r1.iters == r0.iters
+    np.testing.assert_array_equal(r1.assign, r0.assign)
+    np.testing.assert_array_equal(r1.objective, r0.objective)
+    np.testing.assert_array_equal(C1, C0)
+    assert r1.stats["fmas_exec"] < r1.stats["fmas"] == r0.stats["fmas"]
