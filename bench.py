@@ -553,7 +553,7 @@ def run_batched(args, world, rank, local, dist):
         e2e = {"value": docs_done / e_dt, "unit": UNIT,
                "h2d_bytes_per_step": int(sum(8 * (d.n_docs + 1) + 8 * d.nnz for d, _, _ in inst)),
                "d2h_bytes_per_step": int(4 * n_total + 8 * W.max_iter * len(inst)), "host_memory": "pinned"}
-    pk = peaks()
+    pk = peaks(device_sm_count(local))
     ach = 2.0 * fmas / (loop_ms / 1e3) / 1e12 if loop_ms > 0 else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -578,6 +578,7 @@ def run_batched(args, world, rank, local, dist):
                                shapes=st["shape_instances"] if st else None),
                 "roofline": {"bound": "alu", "achieved": ach, "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
                              "frac": ach / pk["fp32_tflops"] if ach else None, "traffic": None,
+                             "peak_source": pk["fp32_source"],
                              "kernel": "whole iteration loop (all kernels; a lower bound for the scoring kernel)",
                              "loop_ms_per_step": loop_ms / args.steps},
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": None}
