@@ -586,12 +586,13 @@ def run_batched(args, world, rank, local, dist):
 
 
 # ------------------------------------------------------------------ serving form
-def serving_session(W, local: int, window: float, tau: float) -> dict:
+def serving_session(W, local: int, window: float, tau: float, rates=None) -> dict:
     """Serving form: open-loop Poisson arrivals against skm_server for a fixed window on a
     resident BF16 centroid set under the workload's device budget. Returns the latency,
-    throughput and admission figures."""
-    import math
-
+    throughput and admission figures at the workload's offered rate; with `rates`, also one
+    window per rate (a fresh server each, same resident centroids) and the largest rate the
+    server sustained: every assignment served and at most 10% of clustering jobs left waiting
+    at the end of the window."""
     import torch
 
     from paper_2108_00895_gb300 import skm, synth
@@ -606,6 +607,29 @@ def serving_session(W, local: int, window: float, tau: float) -> dict:
                                    stream=stream.cuda_stream, device=local)
     resident.set_centroids(C)
     del C
+    try:
+        out = _serving_window(W, local, window, tau, resident, pool, W.rate, True)
+        if rates:
+            sweep = []
+            for r in rates:
+                o = _serving_window(W, local, window, tau, resident, pool, float(r), False)
+                o.pop("queue_depth")
+                o.pop("clocks")
+                sweep.append(dict(rate=float(r), **o))
+            out["rate_sweep"] = sweep
+            ok = [o["rate"] for o in sweep
+                  if o["assign_done"] == o["assign_requests"] and (o["fit_deferred_fraction"] or 0.0) <= 0.1]
+            out["sustained_rate"] = max(ok) if ok else None
+    finally:
+        resident.close()
+    return out
+
+
+def _serving_window(W, local, window, tau, resident, pool, rate, sample_clocks) -> dict:
+    """One open-loop window at `rate` requests/s on a fresh server over `resident`."""
+    import math
+
+    from paper_2108_00895_gb300 import skm, synth
     budget = int(W.budget_gb * (1 << 30))
     srv = skm.Server(resident, budget, n_job_slots=2, max_batch_docs=65536, max_batch_nnz=65536 * 300,
                      job_precision="bf16", job_prune="ncc", tau=tau, device=local)
@@ -628,15 +652,16 @@ def serving_session(W, local: int, window: float, tau: float) -> dict:
         srv.wait(t)
     srv.wait(srv.submit_fit(synth.Csr(rp[:10001], col[:rp[10000]], val[:rp[10000]], pool.n_terms), 64,
                             np.arange(64, dtype=np.int32), 2))
-    clocks = ClockSampler(local)
-    clocks.start()
+    clocks = ClockSampler(local) if sample_clocks else None
+    if clocks:
+        clocks.start()
     tickets = []
     depth = []          # (seconds since start, assignments queued, jobs queued, jobs running)
     t0 = time.perf_counter()
     t_next = 0.0
     last_probe = -1.0
     while True:
-        t_next += rng.exponential(1.0 / W.rate)
+        t_next += rng.exponential(1.0 / rate)
         if t_next > window:
             break
         now = time.perf_counter() - t0
@@ -676,16 +701,15 @@ def serving_session(W, local: int, window: float, tau: float) -> dict:
             cl_docs += n * res["iters"]
         elif res["state"] == "rejected":
             rejected += 1
-    clk = clocks.stop()
+    clk = clocks.stop() if clocks else None
     srv.close()
-    resident.close()
     pct = lambda v, q: float(np.percentile(v, q)) if len(v) else None
     n_assign = sum(1 for k_, _, _ in tickets if k_ == "assign")
     n_fit = len(tickets) - n_assign
     return {"window_s": window, "assign_requests": n_assign, "assign_done": len(lat_a),
             "assign_p50_ms": pct(lat_a, 50), "assign_p99_ms": pct(lat_a, 99),
             "assign_docs_per_s": docs_a / t_drain,
-            "offered_assign_docs_per_s": sum(n for k_, n, _ in tickets if k_ == "assign") / window,
+            "offered_rate": rate, "offered_assign_docs_per_s": sum(n for k_, n, _ in tickets if k_ == "assign") / window,
             "fit_requests": n_fit, "fit_done": done_f, "fit_deferred_at_end": deferred,
             "fit_deferred_fraction": deferred / n_fit if n_fit else None,
             "fit_rejected": rejected, "fit_rejected_fraction": rejected / n_fit if n_fit else None,
@@ -704,7 +728,8 @@ def run_serving(args, world, rank, local, dist):
     W = workloads.SERVING
     torch.cuda.set_device(torch.device("cuda", local))
     skm.load()
-    sv = serving_session(W, local, args.serve_seconds, args.tau)
+    rates = [float(r) for r in args.serve_rates.split(",")] if args.serve_rates else None
+    sv = serving_session(W, local, args.serve_seconds, args.tau, rates)
     clk = sv.pop("clocks")
     line = {"metric": "serving docs assigned/s; p50/p99 assignment latency (ms)", "value": sv["assign_docs_per_s"],
             "unit": "docs/s", "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": 1e3 * sv["drain_seconds"],
@@ -726,6 +751,8 @@ def main():
     ap.add_argument("--workload", choices=["large", "medium", "small", "tweets", "abstracts", "batched", "serving"],
                     default="large")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving window (open loop)")
+    ap.add_argument("--serve-rates", default="250,500,1000,2000,4000",
+                    help="serving workload: also one window per offered rate (requests/s, comma list; '' = none)")
     ap.add_argument("--tau", type=float, default=1e-4)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
