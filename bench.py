@@ -388,7 +388,10 @@ def run_ours(args, w, world, rank, local, dist):
                                 "score_ms_per_step": agg["ms_score"] / args.steps,
                                 "head_ms_per_step": agg["ms_head"] / args.steps,
                                 "decide_ms_per_step": agg["ms_decide"] / args.steps,
-                                "update_ms_per_step": agg["ms_update"] / args.steps}}
+                                "update_ms_per_step": agg["ms_update"] / args.steps,
+                                "index_query_ms_per_step": agg["ms_query"] / args.steps,
+                                "index_build_ms_per_step": agg["ms_index"] / args.steps,
+                                "index_docs_per_step": agg["index_docs"] / args.steps}}
 
     cpu = None
     checks = {}

@@ -18,7 +18,7 @@ namespace skm {
 // 32 at a time and broadcast by shuffle.
 // ------------------------------------------------------------------------------------
 template <typename CT, int NV, bool COLLECT>
-__global__ void __launch_bounds__(256) k_score(ScoreArgs a) {
+__device__ __forceinline__ void score_slice(const ScoreArgs &a) {
     constexpr int EPV = 16 / (int)sizeof(CT);   // elements per 16-byte vector
     constexpr int J = NV * EPV;                  // columns per lane
     constexpr int KS = 32 * J;                   // columns per slice
@@ -52,6 +52,20 @@ __global__ void __launch_bounds__(256) k_score(ScoreArgs a) {
         slice_topt_write<CT, NV>(acc, j0, lane, a.ncols, a.col_ids, a.part_s, a.part_j,
                                  ((int64_t)slice * n_total + gpos) * TOPT);
     }
+}
+
+template <typename CT, int NV, bool COLLECT>
+__global__ void __launch_bounds__(256) k_score(ScoreArgs a) {
+    score_slice<CT, NV, COLLECT>(a);
+}
+
+// The FP32 shape with 512-column slices (short documents), compiled for four resident blocks
+// (64 registers a thread): with that budget the compiler keeps more of the row gathers in
+// flight than with its own choice (60), 13% faster on tweets-like documents; the other
+// shapes are faster with the compiler's choice.
+template <bool COLLECT>
+__global__ void __launch_bounds__(256, 4) k_score_f32w(ScoreArgs a) {
+    score_slice<float, 4, COLLECT>(a);
 }
 
 // k_score with sparse rows: a KS-float scratch and a list staging buffer per warp (dynamic
@@ -133,7 +147,10 @@ static cudaError_t launch_score_t(const ScoreArgs &a, int precision, int slice_c
         switch (slice_cols) {
             case 128: SKM_SCORE(float, 1);
             case 256: SKM_SCORE(float, 2);
-            case 512: SKM_SCORE(float, 4);
+            case 512:
+                if (sp) k_score_sparse<float, 4, COLLECT><<<grid, 256, smem, st>>>(a, *sp);
+                else k_score_f32w<COLLECT><<<grid, 256, 0, st>>>(a);
+                break;
             default: return cudaErrorInvalidValue;
         }
     } else {

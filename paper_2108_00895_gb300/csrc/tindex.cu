@@ -260,31 +260,139 @@ __global__ void __launch_bounds__(TI_NB) k_ti_mtab(const uint32_t *hist, const i
 }
 
 // ------------------------------------------------------------------------------------
-// Build pass 3: one warp per row t. Reads only the nonzeros (the bitmap says where) in two
-// passes: the first counts each level's entries per m bucket (bucket b holds m in
-// (2^(b-1), 2^b], the last one m > 64), the second writes (j << 8 | m) bucket by bucket,
-// in centroid order within a bucket (lanes with the same bucket grouped by match_any, the
-// group's offsets kept per warp in shared memory). pbe[(l d + t) TI_MB + b] = end of
-// bucket b in the row's list. A document of n nonzeros has counts <= n, so it walks only
-// the buckets up to n's.
+// Build pass 3: one warp per row t. Each level's list holds (j << 8 | m) bucket by bucket
+// (bucket b holds m in (2^(b-1), 2^b], the last one m > 64), in centroid order within a
+// bucket (lanes with the same bucket grouped by match_any, the group's offsets kept per
+// warp in shared memory). pbe[(l d + t) TI_MB + b] = end of bucket b in the row's list. A
+// document of n nonzeros has counts <= n, so it walks only the buckets up to n's.
+// A row without nonzeros only gets empty bucket ends. A row of at most TI_FILL_CAP
+// nonzeros (most rows: rare terms) is staged: its bitmap words are loaded together, its
+// nonzero positions listed in shared memory, the entries' m bounds looked up 32 at a time
+// and kept, then counted and written from shared memory, so the row costs three dependent
+// rounds of global loads (bitmap, values, bounds). Longer rows read only their nonzero
+// words (the bitmap says where) in two passes, the first counting, the second writing;
+// both paths write the same lists.
 // ------------------------------------------------------------------------------------
 constexpr int TI_FILL_WARPS = 8;
+constexpr int TI_FILL_CAP = 256;   // nonzeros of a staged row
+constexpr int TI_FILL_GW = 8;      // bitmap words a lane loads at a time on the staged path
+
+// Counts (pass 0) or writes (pass 1) one entry per lane for every level: key = m bucket or
+// -1 (no entry); the lanes of a bucket are ranked by match_any in lane order.
+__device__ __forceinline__ void ti_fill_entries(int pass, int L, const uint32_t (&m)[TI_MAXL], int j, uint32_t *at,
+                                                uint32_t *P, int64_t nzC, int64_t base, unsigned below) {
+#pragma unroll
+    for (int l = 0; l < TI_MAXL; ++l) {
+        if (l >= L) break;   // warp-uniform
+        const int key = m[l] ? ti_mbucket(m[l]) : -1;
+        const unsigned grp = __match_any_sync(FULL, key);
+        const bool lead = key >= 0 && (int)(threadIdx.x & 31) == __ffs(grp) - 1;
+        if (pass == 1 && key >= 0)
+            P[(int64_t)l * nzC + base + at[l * TI_MB + key] + __popc(grp & below)] = ((uint32_t)j << 8) | m[l];
+        __syncwarp();
+        if (lead) at[l * TI_MB + key] += __popc(grp);
+        __syncwarp();
+    }
+}
+
+// Bucket counts -> bucket starts (kept in at) and ends (to pbe).
+__device__ __forceinline__ void ti_fill_starts(int L, int32_t d, int64_t t, uint32_t *at, uint32_t *pbe) {
+    const int lane = threadIdx.x & 31;
+    uint32_t start = 0u;
+    if (lane < L * TI_MB) {
+        const int l = lane / TI_MB, b = lane % TI_MB;
+        for (int q = 0; q < b; ++q) start += at[l * TI_MB + q];
+        pbe[((int64_t)l * d + t) * TI_MB + b] = start + at[lane];
+    }
+    __syncwarp();
+    if (lane < TI_MAXL * TI_MB) at[lane] = start;
+    __syncwarp();
+}
 
 __global__ void __launch_bounds__(TI_FILL_WARPS * 32) k_ti_fill(const float *C, int64_t ldc, int32_t d, int32_t k,
                                                                int32_t W, const uint32_t *G, const uint8_t *mtab,
                                                                int L, const int64_t *gptr, int64_t nzC, uint32_t *P,
                                                                uint32_t *pbe) {
     __shared__ uint32_t at_sm[TI_FILL_WARPS][TI_MAXL * TI_MB];
+    __shared__ int32_t jl_sm[TI_FILL_WARPS][TI_FILL_CAP];              // staged row: nonzero positions
+    __shared__ uint8_t ml_sm[TI_FILL_WARPS][TI_MAXL][TI_FILL_CAP];     // and their m bounds per level
     const int lane = threadIdx.x & 31;
-    uint32_t *at = at_sm[threadIdx.x >> 5];
+    const int wib = threadIdx.x >> 5;
+    uint32_t *at = at_sm[wib];
+    int32_t *jl = jl_sm[wib];
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const unsigned below = (1u << lane) - 1u;
     for (int64_t t = warp; t < d; t += nwarps) {
         const float *row = C + t * ldc;
         const int64_t base = gptr[t];
+        const int64_t cnt = gptr[t + 1] - base;
         if (lane < TI_MAXL * TI_MB) at[lane] = 0u;
         __syncwarp();
+        if (cnt == 0) {
+            ti_fill_starts(L, d, t, at, pbe);   // empty lists
+            continue;
+        }
+        if (cnt <= TI_FILL_CAP) {
+            // list the nonzero positions: bitmap words TI_FILL_GW x 32 at a time, in order
+            int n = 0;
+            for (int w0 = 0; w0 < W; w0 += 32 * TI_FILL_GW) {
+                uint32_t g[TI_FILL_GW];
+#pragma unroll
+                for (int u = 0; u < TI_FILL_GW; ++u) {
+                    const int w = w0 + u * 32 + lane;
+                    g[u] = w < W ? __ldg(G + t * W + w) : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < TI_FILL_GW; ++u) {
+                    // lane's word w0 + 32u + lane: its positions after the lower lanes' ones
+                    const int c = __popc(g[u]);
+                    int incl = c;
+#pragma unroll
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const int o = __shfl_up_sync(FULL, incl, off);
+                        if (lane >= off) incl += o;
+                    }
+                    int at_pos = n + incl - c;
+                    uint32_t bits = g[u];
+                    const int jw = (w0 + u * 32 + lane) * 32;
+                    while (bits) {
+                        const int b = __ffs(bits) - 1;
+                        bits &= bits - 1u;
+                        if (at_pos < TI_FILL_CAP) jl[at_pos] = jw + b;
+                        ++at_pos;
+                    }
+                    n += __shfl_sync(FULL, incl, 31);
+                }
+            }
+            n = min(n, TI_FILL_CAP);   // equal to cnt when the row counts match the bitmap
+            __syncwarp();
+            // bounds of 32 entries at a time (values, then the bounds table), counted per bucket
+            for (int e0 = 0; e0 < n; e0 += 32) {
+                const int e = e0 + lane;
+                const int j = e < n ? jl[e] : 0;
+                const int bin = e < n ? ti_bin(__ldg(row + j)) : 0;
+                uint32_t m[TI_MAXL];
+#pragma unroll
+                for (int l = 0; l < TI_MAXL; ++l)
+                    m[l] = (e < n && l < L) ? (uint32_t)__ldg(mtab + ((size_t)l * k + j) * TI_NB + bin) : 0u;
+                if (e < n)
+#pragma unroll
+                    for (int l = 0; l < TI_MAXL; ++l) ml_sm[wib][l][e] = (uint8_t)m[l];
+                ti_fill_entries(0, L, m, j, at, P, nzC, base, below);
+            }
+            ti_fill_starts(L, d, t, at, pbe);
+            for (int e0 = 0; e0 < n; e0 += 32) {
+                const int e = e0 + lane;
+                const int j = e < n ? jl[e] : 0;
+                uint32_t m[TI_MAXL];
+#pragma unroll
+                for (int l = 0; l < TI_MAXL; ++l) m[l] = (e < n && l < L) ? (uint32_t)ml_sm[wib][l][e] : 0u;
+                ti_fill_entries(1, L, m, j, at, P, nzC, base, below);
+            }
+            __syncwarp();
+            continue;
+        }
         for (int pass = 0; pass < 2; ++pass) {
             // the row's bitmap words 32 at a time; the warp visits the nonzero ones
             for (int w0 = 0; w0 < W; w0 += 32) {
@@ -297,32 +405,14 @@ __global__ void __launch_bounds__(TI_FILL_WARPS * 32) k_ti_fill(const float *C, 
                     const int j = (w0 + qw) * 32 + lane;
                     const bool nz = (g >> lane) & 1u;
                     const int bin = nz ? ti_bin(__ldg(row + j)) : 0;
-                    for (int l = 0; l < L; ++l) {
-                        const uint32_t m = nz ? (uint32_t)__ldg(mtab + ((size_t)l * k + j) * TI_NB + bin) : 0u;
-                        const int key = m ? ti_mbucket(m) : -1;
-                        const unsigned grp = __match_any_sync(FULL, key);
-                        const bool lead = key >= 0 && lane == __ffs(grp) - 1;
-                        if (pass == 1 && key >= 0)
-                            P[(int64_t)l * nzC + base + at[l * TI_MB + key] + __popc(grp & below)] =
-                                ((uint32_t)j << 8) | m;
-                        __syncwarp();
-                        if (lead) at[l * TI_MB + key] += __popc(grp);
-                        __syncwarp();
-                    }
+                    uint32_t m[TI_MAXL];
+#pragma unroll
+                    for (int l = 0; l < TI_MAXL; ++l)
+                        m[l] = (nz && l < L) ? (uint32_t)__ldg(mtab + ((size_t)l * k + j) * TI_NB + bin) : 0u;
+                    ti_fill_entries(pass, L, m, j, at, P, nzC, base, below);
                 }
             }
-            if (pass == 0) {
-                // counts -> bucket starts; the ends go to pbe
-                uint32_t start = 0u;
-                if (lane < L * TI_MB) {
-                    const int l = lane / TI_MB, b = lane % TI_MB;
-                    for (int q = 0; q < b; ++q) start += at[l * TI_MB + q];
-                    pbe[((int64_t)l * d + t) * TI_MB + b] = start + at[lane];
-                }
-                __syncwarp();
-                if (lane < TI_MAXL * TI_MB) at[lane] = start;
-                __syncwarp();
-            }
+            if (pass == 0) ti_fill_starts(L, d, t, at, pbe);
         }
     }
 }
