@@ -754,7 +754,7 @@ def main():
     ap.add_argument("--workload", choices=["large", "medium", "small", "tweets", "abstracts", "batched", "serving"],
                     default="large")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving window (open loop)")
-    ap.add_argument("--serve-rates", default="250,500,1000,2000,4000",
+    ap.add_argument("--serve-rates", default="50,100,250,500,1000,2000,4000",
                     help="serving workload: also one window per offered rate (requests/s, comma list; '' = none)")
     ap.add_argument("--tau", type=float, default=1e-4)
     ap.add_argument("--no-e2e", action="store_true")

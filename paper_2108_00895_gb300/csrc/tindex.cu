@@ -461,6 +461,20 @@ __device__ __forceinline__ void ti_add8(uint32_t (&c)[TI_PLANES], const uint32_t
     }
 }
 
+// The exact double of a float by integer operations (sign, exponent rebiased from 127 to
+// 1023, significand shifted to the top of the 52-bit field); zero, subnormal and non-finite
+// values take the conversion instruction. The FP64 pipe of this GPU is narrow; the candidate
+// scores would otherwise spend two of its operations per product on conversions.
+__device__ __forceinline__ double ti_f2d(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xffu;
+    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+    if ((u & 0x7fffffffu) == 0u) return __longlong_as_double((long long)sign);
+    if (e == 0u || e == 0xffu) return (double)f;
+    return __longlong_as_double((long long)(sign | ((unsigned long long)(e + 896u) << 52) |
+                                            ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+
 struct TiWarpSmem {
     int32_t *t;
     float *x;
@@ -559,8 +573,8 @@ __global__ void __launch_bounds__(TI_WARPS * 32, 4) k_ti_query(TiQueryArgs a) {
             double s = 0.0, ss = 0.0;
             if (lane == 0)
                 for (int p = 0; p < nnz; ++p) {
-                    const double x = (double)sm.x[p];
-                    s = fma(x, (double)sm.cb0[p], s);
+                    const double x = ti_f2d(sm.x[p]);
+                    s = fma(x, ti_f2d(sm.cb0[p]), s);
                     ss = fma(x, x, ss);
                 }
             sb = __shfl_sync(FULL, s, 0);
@@ -715,7 +729,7 @@ __global__ void __launch_bounds__(TI_WARPS * 32, 4) k_ti_query(TiQueryArgs a) {
                     v[u] = p0 + u < nnz ? __ldg(a.C32 + (int64_t)sm.t[p0 + u] * a.ldc + j) : 0.f;
 #pragma unroll
                 for (int u = 0; u < 8; ++u)
-                    if (p0 + u < nnz) acc = fma((double)sm.x[p0 + u], (double)v[u], acc);
+                    if (p0 + u < nnz) acc = fma(ti_f2d(sm.x[p0 + u]), ti_f2d(v[u]), acc);
             }
             n_prod += (unsigned long long)nnz;
             ++n_sims;
