@@ -45,6 +45,14 @@ LARGE_FULL_PASS_ALG_BYTES = 7.43e9
 LARGE_FULL_PASS_SCOPE = ("one full-pass k_score launch of step 1 (2M documents x 10,000 centroids, all nonzeros "
                          f"gathered); algorithmic bytes of that launch {LARGE_FULL_PASS_ALG_BYTES:.3g}")
 
+# With the head on the tensor cores (the default), one full pass of the first step is 20
+# chunks of k_head_rows + k_head_gemm + k_score over the tail nonzeros; DRAM bytes of the 20
+# launches of each, from the capture in the same profile (second section).
+LARGE_HEAD_FULL_PASS_TRAFFIC = {"k_score (tail)": 930.4e9 + 1.3e9, "k_head_gemm": 4.8e9 + 39.8e9,
+                                "k_head_rows": 1.0e9 + 2.9e9}
+LARGE_HEAD_FULL_PASS_SCOPE = ("one full pass of step 1 (2M documents x 10,000 centroids), 20 launches of each kernel; "
+                              f"algorithmic bytes of the pass {LARGE_FULL_PASS_ALG_BYTES:.3g}")
+
 METRIC = "docs assigned/s per iteration"
 UNIT = "docs/s"
 FP32_LANES_PER_SM = 128
@@ -373,6 +381,8 @@ def run_ours(args, w, world, rank, local, dist):
                 "frac": achieved_tf / pk["fp32_tflops"] if achieved_tf else None,
                 "traffic": LARGE_FULL_PASS_TRAFFIC if default_large and not agg.get("head_terms") else None,
                 "traffic_scope": LARGE_FULL_PASS_SCOPE if default_large and not agg.get("head_terms") else None,
+                "traffic_full_pass": (dict(LARGE_HEAD_FULL_PASS_TRAFFIC, scope=LARGE_HEAD_FULL_PASS_SCOPE)
+                                      if default_large and agg.get("head_terms") and args.head_terms == 0 else None),
                 "kernel": ("scoring pass: k_head_gemm (tensor cores, the collection's most frequent terms) + "
                            "k_score (gathers over the other nonzeros, top-4 per slice)"
                            if agg.get("head_terms") else

@@ -55,6 +55,22 @@ def test_candidates_contain_oracle_candidates_and_every_high_similarity(skm, sha
     w = SHAPES[shape]
     docs = w.corpus()
     C = _trained(docs, w.k, w.init_ids())
+    _check_candidates(skm, w, docs, C)
+
+
+def test_candidates_with_rows_on_both_fill_paths(skm):
+    """k = 600: the frequent terms' rows hold more than 256 nonzeros (lists filled from the
+    bitmap in two passes), the rare terms' rows fewer (staged fill); both give the oracle's
+    candidates."""
+    w = workloads.TWEETS.scaled(n_docs=6000, n_terms=20000, k=600, max_iter=15, shift_tol=-1.0)
+    docs = w.corpus()
+    C = _trained(docs, w.k, w.init_ids(), iters=2)
+    row_nz = (C != 0).sum(axis=1)
+    assert (row_nz > 256).sum() >= 10 and ((row_nz > 0) & (row_nz <= 256)).sum() >= 1000
+    _check_candidates(skm, w, docs, C)
+
+
+def _check_candidates(skm, w, docs, C):
     S = oracle.scores(docs, C)
     xn = np.sqrt(np.add.reduceat(docs.values.astype(np.float64) ** 2, docs.row_ptr[:-1]))
     overlap = oracle.scores(docs, (C != 0).astype(np.float32)) > 0   # shares a nonzero term
