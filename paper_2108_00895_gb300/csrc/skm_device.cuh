@@ -265,6 +265,43 @@ __device__ __forceinline__ void slice_accumulate_sparse(int64_t beg, int64_t end
 // The slice's best TOPT (score, centroid id) of a warp's accumulators, written by lanes
 // 0..TOPT-1 to part_s/part_j[o + lane]. Columns at or beyond ncols are ignored; col_ids maps
 // a column to its centroid id (NULL: identity).
+// The warp's best TOPT over the lanes' best-first lists, in TOPT rounds: the largest score,
+// then the smallest id among the lanes that hold it; the winning lane drops its head. Scores
+// are non-negative, so their bit patterns order like their values and one warp reduction
+// finds the largest; an empty entry (-inf, INT32_MAX) and a score of +0 both count as 0, and
+// the id decides, as in `better`. Every lane ends with the result in ls, lj, best first.
+__device__ __forceinline__ void topt_warp_select(float (&ls)[TOPT], int (&lj)[TOPT]) {
+    const int lane = threadIdx.x & 31;
+    float rs[TOPT];
+    int rj[TOPT];
+#pragma unroll
+    for (int q = 0; q < TOPT; ++q) {
+        const uint32_t key = ls[0] > 0.f ? __float_as_uint(ls[0]) : 0u;
+        const uint32_t kmax = __reduce_max_sync(FULL, key);
+        const bool top = key == kmax;
+        const unsigned holders = __ballot_sync(FULL, top);
+        uint32_t jm = (uint32_t)lj[0];
+        if (__popc(holders) > 1 && top) jm = __reduce_min_sync(holders, (uint32_t)lj[0]);
+        const int win = __ffs(__ballot_sync(FULL, top && (uint32_t)lj[0] == jm)) - 1;
+        rs[q] = __shfl_sync(FULL, ls[0], win);
+        rj[q] = __shfl_sync(FULL, lj[0], win);
+        if (lane == win) {
+#pragma unroll
+            for (int r = 0; r + 1 < TOPT; ++r) {
+                ls[r] = ls[r + 1];
+                lj[r] = lj[r + 1];
+            }
+            ls[TOPT - 1] = -INFINITY;
+            lj[TOPT - 1] = INT32_MAX;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < TOPT; ++q) {
+        ls[q] = rs[q];
+        lj[q] = rj[q];
+    }
+}
+
 template <typename CT, int NV>
 __device__ __forceinline__ void slice_topt_write(const float2 (&acc)[NV * 16 / (int)sizeof(CT) / 2], int64_t j0,
                                                  int lane, int32_t ncols, const int32_t *col_ids, float *part_s,
@@ -286,7 +323,7 @@ __device__ __forceinline__ void slice_topt_write(const float2 (&acc)[NV * 16 / (
             }
         }
     }
-    topt_warp_merge(ls, lj);
+    topt_warp_select(ls, lj);
     if (lane < TOPT) {
         float s = ls[0];
         int j = lj[0];

@@ -57,21 +57,6 @@ __device__ __forceinline__ void topt_merge2(float (&as)[TOPT], int (&aj)[TOPT],
 #undef SKM_CSWAP
 }
 
-// Merge the lists of all 32 lanes (butterfly); every lane ends with the warp's best TOPT.
-__device__ __forceinline__ void topt_warp_merge(float (&ls)[TOPT], int (&lj)[TOPT]) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        float os[TOPT];
-        int oj[TOPT];
-#pragma unroll
-        for (int q = 0; q < TOPT; ++q) {
-            os[q] = __shfl_xor_sync(FULL, ls[q], off);
-            oj[q] = __shfl_xor_sync(FULL, lj[q], off);
-        }
-        topt_merge2(ls, lj, os, oj);
-    }
-}
-
 // ---------------------------------------------------------------- bf16 widening
 __device__ __forceinline__ float bf16lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
