@@ -302,11 +302,34 @@ __device__ __forceinline__ void topt_warp_select(float (&ls)[TOPT], int (&lj)[TO
     }
 }
 
+// The slice's best TOPT (score, centroid id) to part_s / part_j [o, o + TOPT). Only columns
+// that can be among them are sorted into the lanes' lists: with T the TOPT-th largest of the
+// 32 lanes' maxima, TOPT columns (those maxima) score at least T, so every column of the
+// result does too. Scores are non-negative and compare as their bit patterns. When fewer than
+// TOPT lanes hold a positive score (T = 0), every column goes into the lists.
 template <typename CT, int NV>
 __device__ __forceinline__ void slice_topt_write(const float2 (&acc)[NV * 16 / (int)sizeof(CT) / 2], int64_t j0,
                                                  int lane, int32_t ncols, const int32_t *col_ids, float *part_s,
                                                  int32_t *part_j, int64_t o) {
     constexpr int EPV = 16 / (int)sizeof(CT);
+    auto key_of = [&](int u, int e) -> uint32_t {
+        const int64_t c = j0 + u * 32 * EPV + lane * EPV + e;
+        const int qq = (u * EPV + e) >> 1;
+        const float sc = (e & 1) ? acc[qq].y : acc[qq].x;
+        return (c < ncols && sc > 0.f) ? __float_as_uint(sc) : 0u;
+    };
+    uint32_t mm = 0u;
+#pragma unroll
+    for (int u = 0; u < NV; ++u)
+#pragma unroll
+        for (int e = 0; e < EPV; ++e) mm = max(mm, key_of(u, e));
+    uint32_t T = 0u;
+#pragma unroll
+    for (int q = 0; q < TOPT; ++q) {
+        T = __reduce_max_sync(FULL, mm);
+        const unsigned h = __ballot_sync(FULL, mm == T);
+        if (lane == __ffs(h) - 1) mm = 0u;
+    }
     float ls[TOPT];
     int lj[TOPT];
 #pragma unroll
@@ -316,7 +339,7 @@ __device__ __forceinline__ void slice_topt_write(const float2 (&acc)[NV * 16 / (
 #pragma unroll
         for (int e = 0; e < EPV; ++e) {
             const int64_t c = j0 + u * 32 * EPV + lane * EPV + e;
-            if (c < ncols) {
+            if (c < ncols && (T == 0u || key_of(u, e) >= T)) {
                 const int id = col_ids ? __ldg(col_ids + c) : (int)c;
                 const int qq = (u * EPV + e) >> 1;
                 topt_insert(ls, lj, (e & 1) ? acc[qq].y : acc[qq].x, id);
@@ -325,11 +348,11 @@ __device__ __forceinline__ void slice_topt_write(const float2 (&acc)[NV * 16 / (
     }
     topt_warp_select(ls, lj);
     if (lane < TOPT) {
-        float s = ls[0];
+        float sq = ls[0];
         int j = lj[0];
 #pragma unroll
-        for (int q = 1; q < TOPT; ++q) if (lane == q) { s = ls[q]; j = lj[q]; }
-        part_s[o + lane] = s;
+        for (int q = 1; q < TOPT; ++q) if (lane == q) { sq = ls[q]; j = lj[q]; }
+        part_s[o + lane] = sq;
         part_j[o + lane] = j;
     }
 }
