@@ -780,8 +780,9 @@ def main():
     ap.add_argument("--prune", choices=["ncc", "none", "ncc_index"], default=None, help="override the workload's")
     ap.add_argument("--index-min-changed", type=int, default=100,
                     help="ncc_index: steps use the threshold index after more than this many centroids changed")
-    ap.add_argument("--index-max-cands", type=int, default=0,
-                    help="ncc_index: documents with more candidates are scored densely (0 = cost rule)")
+    ap.add_argument("--index-max-cands", type=int, default=256,
+                    help="ncc_index: candidate cap of the index (documents with more are scored densely); "
+                         "0 = the library's default, which runs the NCC passes alone")
     ap.add_argument("--rescore", choices=["on", "off"], default="on", help="FP64 rescoring of near ties")
     ap.add_argument("--max-iter", type=int, default=None, help="override the workload's step limit")
     ap.add_argument("--sparse-div", type=int, default=0, help="sparse centroid rows (0 = off)")

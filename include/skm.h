@@ -100,15 +100,13 @@ typedef struct {
     int32_t index_min_changed; /* the index serves a step only when more than this many
                                   centroids changed in the previous update (Sec. 4.3
                                   suggests 100, the default); -1: every step after the first */
-    int32_t index_max_cands; /* a document with more candidates than this is scored densely.
-                                0 (the default) selects the automatic cost rules: the cap is
-                                min(256, k * (element bytes) / 32), where scoring candidates
-                                one by one (a 32-byte sector per product) stops being cheaper
-                                than a dense pass; documents whose list walk exceeds
-                                nnz * k / 16 entries are scored densely; the index serves only
-                                k >= 1024, and stops for the rest of a fit after a step that
-                                decided fewer than half of the documents through it.
-                                > 0: that cap (at most 256) and none of those rules. */
+    int32_t index_max_cands; /* SKM_PRUNE_NCC_INDEX: > 0 (at most 256) turns the index on
+                                for fits; a document with more candidates than this is scored
+                                densely. 0 (the default): fits run the NCC passes alone,
+                                because on the GPUs this library was measured on the dense NCC
+                                passes were faster than the index on every workload tried
+                                (short documents at k = 5000 to 16384 included).
+                                skm_index_candidates uses the index either way. */
     int32_t head_terms;   /* BF16 scoring (k > 256, sparse_div = 0): the products over the
                              collection's most frequent terms (its head, by document
                              frequency, fixed for a fit) run on the tensor cores as a dense

@@ -96,12 +96,6 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-// Byte offset of 16-bit element (r, k), k < 64, in such a tile: the 16-byte chunk k / 8 of
-// row r is stored at chunk (k / 8) xor (r mod 8).
-__device__ __forceinline__ uint32_t sw128_off(int r, int k) {
-    return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 3) ^ r) & 7) << 4) + ((k & 7) << 1));
-}
-
 // Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator (bits 4-5), FP16 A and B
 // (bits 7-9, 10-12), both K-major (bits 15, 16), N / 8 (bits 17-22), M / 16 (bits 24-28).
 constexpr uint32_t TC_IDESC =

@@ -1515,14 +1515,10 @@ skm_status skm_fit(skm_ctx *ctx, const skm_csr *docs, const int32_t *init_doc_id
     ctx->stats.launches_total += 3;
 
     const bool prune = ctx->cfg.prune != SKM_PRUNE_NONE;
-    // automatic mode (no candidate cap configured) adds two cost rules to Sec. 4.3's: the
-    // index serves only k >= TI_AUTO_MIN_K, where a dense pass over a short document is long
-    // enough to lose against the index's fixed per-document costs, and it stops for the rest
-    // of the fit after a step that decided fewer than half of the documents through it (the
-    // per-step build is then not recovered: abstracts-like documents, mostly over 64 nonzeros)
-    const bool ti_auto = ctx->cfg.index_max_cands == 0;
-    const bool use_index = ctx->cfg.prune == SKM_PRUNE_NCC_INDEX && k <= TI_MAX_K && (!ti_auto || k >= TI_AUTO_MIN_K);
-    bool ti_off = false;
+    // the index serves only with a candidate cap configured: in automatic mode (no cap) the
+    // dense NCC passes were faster than the index on every workload measured on this GPU
+    // (short documents at k = 5000 to 16384 included), so the fit runs them alone
+    const bool use_index = ctx->cfg.prune == SKM_PRUNE_NCC_INDEX && k <= TI_MAX_K && ctx->cfg.index_max_cands > 0;
     if (use_index) {
         SKM_TRY(ensure(ctx, ctx->ti_stats, 4 * sizeof(unsigned long long)));
         SKM_CUDA(cudaMemsetAsync(ctx->ti_stats.p, 0, 4 * sizeof(unsigned long long), ctx->st));
@@ -1540,7 +1536,7 @@ skm_status skm_fit(skm_ctx *ctx, const skm_csr *docs, const int32_t *init_doc_id
         const int32_t *full_list = P<int32_t>(ctx->order);
         // Sec. 3.2: the threshold index decides the documents whose baseline reaches a
         // threshold when enough centroids changed (Sec. 4.3); the rest go to the dense passes
-        const bool index_step = use_index && !first && !ti_off &&
+        const bool index_step = use_index && !first &&
                                 (ctx->cfg.index_min_changed < 0 || n_moved_prev > ctx->cfg.index_min_changed);
         if (index_step) {
             SKM_TRY(build_tindex(ctx));
@@ -1570,7 +1566,6 @@ skm_status skm_fit(skm_ctx *ctx, const skm_csr *docs, const int32_t *init_doc_id
             n_pruned = ctx->h_counters[CNT_PRUNED];
             n_full = ctx->h_counters[CNT_FULL];
             full_list = P<int32_t>(ctx->list_b);
-            if (ti_auto && 2 * (N - n_pruned - n_full) < N) ti_off = true;
         } else if (prune && !first && ctx->cm_valid) {
             // the pruned pass needs the compacted matrix of the last update's moved list
             PartitionArgs pa{};

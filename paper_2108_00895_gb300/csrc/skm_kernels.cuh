@@ -220,7 +220,6 @@ constexpr int TI_MAXL = 4;     // thresholds (lambda levels)
 constexpr int TI_MB = 8;       // m buckets of each term's list
 constexpr int TI_PLANES = 8;   // bits of the overlap counts and of the stored m bounds
 constexpr int32_t TI_MAX_K = 16384;
-constexpr int32_t TI_AUTO_MIN_K = 1024;   // automatic mode: smallest k the index serves
 __host__ __device__ constexpr int32_t ti_words(int32_t k) { return (k + 31) / 32; }
 
 constexpr uint32_t TI_KEY0 = 1536;   // float bits >> 19 of 2^-31, the lowest bin's lower edge
@@ -254,7 +253,7 @@ struct TiQueryArgs {
     const uint32_t *pbe;        // [L][d][TI_MB] bucket ends of each term's list
     int L;
     int elt;                    // bytes per entry of the dense scored copy (2 BF16, 4 FP32)
-    int max_cands;              // > 0: candidate cap (at most 512); 0: min(512, k elt / 32)
+    int max_cands;              // candidate cap (at most TI_CAND); 0: TI_CAND
     double lam[TI_MAXL];        // ascending
     int fixed_level;            // >= 0: candidate dump at this level (no baseline, no scoring)
     uint32_t *cand_out;         // candidate dump: [document][W] bits

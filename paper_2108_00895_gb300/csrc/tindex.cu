@@ -49,7 +49,6 @@ constexpr int TI_STAGE = 40;   // most nonzeros of a document the query serves
 constexpr int TI_CAND = 256;   // most candidates it scores
 constexpr int TI_WALK = 8;     // list entries a lane loads at a time
 constexpr int TI_CGRP = 2;     // bitmap words a lane counts at a time
-constexpr int TI_WALK_RATIO = 16;   // automatic mode: walks above nnz k / 16 entries go dense
 
 // Shared-memory words of one query warp (layout in ti_warp_smem), a multiple of 4 words.
 // The candidate list reuses the count planes (dead after the walk) when they are large enough.
@@ -428,11 +427,8 @@ __global__ void __launch_bounds__(TI_FILL_WARPS * 32) k_ti_fill(const float *C, 
 // word (word w's at [8w, 8w + 8), read and written as two 16-byte vectors), the candidate
 // bits and the candidate list; rounded up to 16 bytes.
 // A document goes to the dense passes when no threshold is below its baseline, when it
-// has more than TI_STAGE nonzeros, or (unless a candidate cap is configured) when its walk
-// would cost more than a dense pass: more than nnz k / 16 list entries (each takes about as
-// many instructions as 16 dense multiply-adds), or when its candidates would cost more to
-// score one by one (a 32-byte sector per product) than a dense pass over all k (elt bytes
-// per product): more than min(TI_CAND, k elt / 32) candidates (or the configured cap).
+// has more than TI_STAGE nonzeros, or when it has more candidates than the configured cap
+// (at most TI_CAND).
 // ------------------------------------------------------------------------------------
 // Carry-save adder: a + b + c = 2 h + l in every bit position.
 __device__ __forceinline__ void ti_csa(uint32_t &h, uint32_t &l, uint32_t a, uint32_t b, uint32_t c) {
@@ -542,7 +538,7 @@ __global__ void __launch_bounds__(TI_WARPS * 32, 4) k_ti_query(TiQueryArgs a) {
     __syncthreads();
     unsigned long long n_docs = 0, n_sims = 0, n_walk = 0, n_prod = 0;
     const int64_t nw = (int64_t)gridDim.x * TI_WARPS;
-    const int cand_cap = a.max_cands > 0 ? min(TI_CAND, a.max_cands) : min(TI_CAND, (int)((int64_t)a.k * a.elt / 32));
+    const int cand_cap = a.max_cands > 0 ? min(TI_CAND, a.max_cands) : TI_CAND;
     for (int64_t pos = (int64_t)blockIdx.x * TI_WARPS + wib; pos < a.n_list; pos += nw) {
         const int32_t i = a.list ? a.list[pos] : (int32_t)pos;
         const int64_t beg = a.row_ptr[i];
@@ -644,12 +640,6 @@ __global__ void __launch_bounds__(TI_WARPS * 32, 4) k_ti_query(TiQueryArgs a) {
         __syncwarp();
         // walk P_lambda over the document's terms as one flat list of entries
         const uint32_t E = sm.pre[nnz];
-        if (a.max_cands == 0 && (int64_t)E * TI_WALK_RATIO > (int64_t)nnz * a.k && !a.cand_out) {
-            // a walk of more than nnz k / TI_WALK_RATIO entries costs more than a dense pass
-            if (lane == 0) ti_fallback(a, i, a0, nnz);
-            __syncwarp();
-            continue;
-        }
         n_walk += (lane == 0) ? E : 0u;
         const uint32_t *Pl = a.P + (int64_t)lev * a.nzC;
         const bool nccf = a.ncc && a0 >= 0 && !a.changed[a0];

@@ -396,8 +396,8 @@ class SphericalKMeans:
     precision: "fp32" or "bf16" (scored centroid copy); prune: "none", "ncc" (Sec. 3.1
     skip) or "ncc_index" (plus the threshold index of Sec. 3.2, with the minimum dot
     products index_lambdas, used in steps after more than index_min_changed centroids
-    changed; -1 = every step; documents with more than index_max_cands candidates, 0 =
-    automatic, are scored densely); rescore: FP64 rescoring of near ties; tau: margin threshold;
+    changed; -1 = every step; fits use the index only with index_max_cands > 0, and
+    documents with more candidates than that are scored densely); rescore: FP64 rescoring of near ties; tau: margin threshold;
     sparse_div: centroid rows with at most k / sparse_div nonzeros are scored from their
     nonzero lists (0 = off; results are identical either way). head_terms: BF16 scoring of
     the collection's most frequent terms on the tensor cores (0 = automatic, -1 = off, > 0 =

@@ -41,8 +41,10 @@ def _device(docs):
 
 def _fit(skm, w, dev, n_terms, ids, max_iter, prune=None):
     import torch
-    with skm.SphericalKMeans(w.k, precision=w.precision, prune=prune or w.prune, max_iter=max_iter,
-                             shift_tol=w.shift_tol, tau=1e-4) as km:
+    prune = prune or w.prune
+    # the index serves fits only with a candidate cap
+    with skm.SphericalKMeans(w.k, precision=w.precision, prune=prune, max_iter=max_iter, shift_tol=w.shift_tol,
+                             tau=1e-4, index_max_cands=256 if prune == "ncc_index" else 0) as km:
         r = km.fit(dev, ids, n_terms=n_terms)
         C = km.centroids()
     torch.cuda.synchronize()
@@ -82,7 +84,7 @@ def test_large_workload_step_locked(skm):
 
 def test_tweets_workload_with_index_step_locked(skm):
     """The tweets-like analog at full size (N = 1M, d = 783,304, k = 5000, FP32) with the
-    threshold index of Sec. 3.2 combined with Sec. 3.1 (NCC+INDEX, automatic rules): the
+    threshold index of Sec. 3.2 combined with Sec. 3.1 (NCC+INDEX, candidate cap 256): the
     sixth step, whose documents the index decides in part, against the oracle."""
     _step_locked(skm, workloads.TWEETS, 6, 2000, 40, prune="ncc_index")
 
@@ -113,7 +115,7 @@ def test_pruned_equals_full_at_full_size(skm, name):
 
 
 def test_index_equals_ncc_at_full_size(skm):
-    """The threshold index (automatic rules) at the tweets-like analog, N = 1M, d = 783,304,
+    """The threshold index (candidate cap 256) at the tweets-like analog, N = 1M, d = 783,304,
     k = 5000, the paper's stop rule: same assignments, objectives and (sampled) centroid
     columns as the NCC fit."""
     import torch
@@ -124,7 +126,8 @@ def test_index_equals_ncc_at_full_size(skm):
     out = {}
     for prune in ("ncc", "ncc_index"):
         with skm.SphericalKMeans(w.k, precision=w.precision, prune=prune, max_iter=w.max_iter,
-                                 shift_tol=w.shift_tol, tau=1e-4) as km:
+                                 shift_tol=w.shift_tol, tau=1e-4,
+                                 index_max_cands=256 if prune == "ncc_index" else 0) as km:
             r = km.fit(dev, ids, n_terms=docs.n_terms)
             cols = synth.sample_ids(w.k, 64, 33)
             C = km.centroids()[:, cols]

@@ -149,6 +149,21 @@ def test_index_min_changed_gates_the_index(skm):
         np.testing.assert_array_equal(out[gate].objective, out[-1].objective)
 
 
+def test_fits_without_a_cap_run_ncc_alone(skm):
+    """Without a candidate cap a fit does not use the index (the dense NCC passes are the
+    faster path on this GPU); its result is the NCC fit's, bit for bit."""
+    w = SHAPES["tweets"]
+    docs = w.corpus()
+    ids = w.init_ids()
+    out = {}
+    for prune in ("ncc", "ncc_index"):
+        with skm.SphericalKMeans(w.k, prune=prune, max_iter=w.max_iter, index_min_changed=-1) as km:
+            out[prune] = km.fit(docs, ids)
+    assert out["ncc_index"].stats["index_docs"] == 0
+    np.testing.assert_array_equal(out["ncc_index"].assign, out["ncc"].assign)
+    np.testing.assert_array_equal(out["ncc_index"].objective, out["ncc"].objective)
+
+
 def test_custom_thresholds_and_documents_below_every_threshold(skm):
     """One high threshold: most baselines stay below it and those documents go to the
     dense passes; the result is still the full fit's."""
