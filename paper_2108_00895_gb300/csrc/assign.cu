@@ -60,8 +60,8 @@ __global__ void __launch_bounds__(256) k_score(ScoreArgs a) {
 }
 
 // The FP32 shape with 512-column slices (short documents), compiled for four resident blocks
-// (64 registers a thread): with that budget the compiler keeps more of the row gathers in
-// flight than with its own choice (60), 13% faster on tweets-like documents; the other
+// (64 registers a thread): with that budget the compiler schedules the row gathers better
+// than with its own choice (scoring of a tweets-like job 349 against 363 ms); the other
 // shapes are faster with the compiler's choice.
 template <bool COLLECT>
 __global__ void __launch_bounds__(256, 4) k_score_f32w(ScoreArgs a) {
