@@ -21,19 +21,21 @@
 // copy's unit roundoff 2^-8, so the bound beta s of the plain BF16 pass still holds, and the
 // absolute part, at most 2^-33 sqrt(nnz) + 2^-25, is added to the decision's threshold.
 //
-// Kernel k_head_gemm: persistent, one CTA of 10 warps per SM. A unit is 256 listed documents
-// (two MMA tiles of M = 128) x 256 columns (N = 256), accumulated in 512 TMEM columns over
-// the h / 64 head blocks; units are taken document pair by document pair, so a pair's rows
-// stay in L2 across its column blocks. The document operand is the dense FP16 head matrix of
-// the listed documents (k_head_rows, written once per scoring pass), the centroid operand the
-// FP16 head matrix of the centroids; TMA brings both (128-byte swizzle, K-major). Warp roles:
-//   - one thread issues the TMA copies of a stage (two 128 x 64 document boxes, one 256 x 64
+// Kernel k_head_gemm: persistent, one CTA of 10 warps per SM. A unit is 128 listed documents
+// (one MMA tile, M = 128) x 256 columns (N = 256), accumulated over the h / 64 head blocks in
+// one of two 256-column TMEM accumulators, so that the products of a unit overlap the
+// draining of the previous one. Units are taken document tile by document tile, so a tile's
+// rows stay in L2 across its column blocks. The document operand is the dense FP16 head
+// matrix of the listed documents (k_head_rows, written once per scoring pass), the centroid
+// operand the FP16 head matrix of the centroids; TMA brings both (128-byte swizzle, K-major).
+// Warp roles:
+//   - one thread issues the TMA copies of a stage (a 128 x 64 document box and a 256 x 64
 //     centroid box);
-//   - one thread issues the tcgen05.mma instructions (4 K-steps x 2 tiles per block) and the
-//     commits that free a stage and announce a finished unit;
-//   - 8 epilogue warps (one per TMEM lane quarter and tile) read the sums with tcgen05.ld and
-//     store them, times 2^-20 and rounded to FP16, to out[position][column].
-// Three stages overlap the loads of a block with the products of the previous ones. Every
+//   - one thread issues the tcgen05.mma instructions (4 K-steps per block) into the unit's
+//     accumulator and the commits that free a stage and announce a finished unit;
+//   - 8 epilogue warps, 4 per accumulator (one per TMEM lane quarter), read the sums with
+//     tcgen05.ld and store them, times 2^-20 and rounded to FP16, to out[position][column].
+// Four stages overlap the loads of a block with the products of the previous ones. Every
 // wait on an mbarrier is bounded: a timeout sets bit 32 of *err, skips the remaining work,
 // waits (bounded) for the products and copies in flight and frees TMEM.
 #include <cuda.h>
@@ -129,15 +131,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *r) {
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Warp roles of k_head_gemm (10 warps): 0-7 epilogue (warp w reads TMEM lane quarter w % 4
-// of tile w / 4), 8 issues the MMAs, 9 issues the TMA copies.
+// of accumulator w / 4), 8 issues the MMAs, 9 issues the TMA copies.
 constexpr int HG_EPI_WARPS = 8;
 constexpr int HG_MMA_WARP = 8;
 constexpr int HG_TMA_WARP = 9;
 constexpr int HG_WARPS = 10;
 constexpr int HG_THREADS = HG_WARPS * 32;
-constexpr int HG_DOCS = 2 * TC_M;               // documents per unit: two MMA tiles
-constexpr int HG_STAGE = 2 * A_BYTES + B_HALF;  // two document tiles + one 256-row centroid tile
-constexpr int HG_STAGES = 3;
+constexpr int HG_DOCS = TC_M;                   // documents per unit: one MMA tile
+constexpr int HG_STAGE = A_BYTES + B_HALF;      // one document tile + one 256-row centroid tile
+constexpr int HG_STAGES = 4;
+constexpr int HG_EPI_PER_BUF = HG_EPI_WARPS / 2;  // epilogue warps per TMEM accumulator
 constexpr int HG_SMEM = HG_STAGES * HG_STAGE + 1024;
 static_assert(HG_STAGE % 1024 == 0, "stages keep the 1024-byte swizzle alignment");
 
@@ -147,7 +150,7 @@ __global__ void __launch_bounds__(HG_THREADS, 1)
     extern __shared__ unsigned char smem_raw[];
     unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                           ~static_cast<uintptr_t>(1023));
-    __shared__ uint64_t full_s[HG_STAGES], empty_s[HG_STAGES], acc_full, acc_empty, end_bar;
+    __shared__ uint64_t full_s[HG_STAGES], empty_s[HG_STAGES], acc_full[2], acc_empty[2], end_bar;
     __shared__ uint32_t tmem_base_sh;
     __shared__ volatile int abort_sh;
     __shared__ uint32_t tma_g, mma_g;        // stage uses with copies issued / their arrival seen
@@ -164,8 +167,10 @@ __global__ void __launch_bounds__(HG_THREADS, 1)
             mbar_init(&full_s[s], 1);
             mbar_init(&empty_s[s], 1);
         }
-        mbar_init(&acc_full, 1);
-        mbar_init(&acc_empty, HG_EPI_WARPS);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], HG_EPI_PER_BUF);
+        }
         mbar_init(&end_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         abort_sh = 0;
@@ -177,35 +182,36 @@ __global__ void __launch_bounds__(HG_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = tmem_base_sh;
     const int kblocks = a.h / TC_KB;
-    const int n_pairs = (a.n + HG_DOCS - 1) / HG_DOCS;
-    const int n_units = n_pairs * a.n_cblk;
+    const int n_tiles = (a.n + HG_DOCS - 1) / HG_DOCS;
+    const int n_units = n_tiles * a.n_cblk;
 
     if (warp == HG_TMA_WARP) {
-        // ---- operands by TMA: stage g holds head block kb of the unit's two document tiles
-        // (rows of the dense head matrix) and of its 256-column block of the centroid head
+        // ---- operands by TMA: stage g holds head block kb of the unit's document tile (rows
+        // of the dense head matrix) and of its 256-column block of the centroid head
         if (lane == 0) {
             uint32_t g = 0;
             for (int u = blockIdx.x; u < n_units && !abort_sh; u += gridDim.x) {
-                const int pair = u / a.n_cblk, cb = u - pair * a.n_cblk;
+                const int tile = u / a.n_cblk, cb = u - tile * a.n_cblk;
                 for (int kb = 0; kb < kblocks; ++kb, ++g) {
                     const int s = g % HG_STAGES;
                     const uint32_t use = g / HG_STAGES;
                     if (use > 0 && !mbar_wait(&empty_s[s], (use - 1) & 1)) { abort_sh = 1; break; }
                     unsigned char *st = sm + s * HG_STAGE;
                     mbar_expect_tx(&full_s[s], HG_STAGE);
-                    tma_load_2d(st, &amap, &full_s[s], kb * TC_KB, pair * HG_DOCS);
-                    tma_load_2d(st + A_BYTES, &amap, &full_s[s], kb * TC_KB, pair * HG_DOCS + TC_M);
-                    tma_load_2d(st + 2 * A_BYTES, &bmap, &full_s[s], kb * TC_KB, cb * TC_N);
+                    tma_load_2d(st, &amap, &full_s[s], kb * TC_KB, tile * HG_DOCS);
+                    tma_load_2d(st + A_BYTES, &bmap, &full_s[s], kb * TC_KB, cb * TC_N);
                     tma_g = g + 1;
                 }
             }
         }
     } else if (warp == HG_MMA_WARP) {
-        // ---- products: per head block, 4 K-steps x 2 tiles of M = 128, N = 256
+        // ---- products: per head block, 4 K-steps of M = 128, N = 256
         if (lane == 0) {
             uint32_t g = 0, v = 0;
             for (int u = blockIdx.x; u < n_units && !abort_sh; u += gridDim.x, ++v) {
-                if (v > 0 && !mbar_wait(&acc_empty, (v - 1) & 1)) { abort_sh = 1; break; }
+                // accumulator v % 2, drained by its epilogue warps after its previous use
+                const int ab = v & 1;
+                if (v >= 2 && !mbar_wait(&acc_empty[ab], ((v >> 1) - 1) & 1)) { abort_sh = 1; break; }
                 tc_fence_after();
                 bool ok = true;
                 for (int kb = 0; kb < kblocks; ++kb, ++g) {
@@ -214,33 +220,31 @@ __global__ void __launch_bounds__(HG_THREADS, 1)
                     if (!mbar_wait(&full_s[s], use & 1)) { ok = false; break; }
                     mma_g = g + 1;
                     tc_fence_after();
-                    const uint32_t a0 = su32(sm + s * HG_STAGE), b0 = a0 + 2 * A_BYTES;
+                    const uint32_t a0 = su32(sm + s * HG_STAGE), b0 = a0 + A_BYTES;
 #pragma unroll
-                    for (int ks = 0; ks < TC_KB / 16; ++ks) {
-                        const uint64_t bd = sw128_desc(b0 + ks * 32);
-#pragma unroll
-                        for (int t = 0; t < 2; ++t)
-                            tc_mma(tmem + t * TC_N, sw128_desc(a0 + t * A_BYTES + ks * 32), bd,
-                                   (kb | ks) != 0 ? 1u : 0u);
-                    }
+                    for (int ks = 0; ks < TC_KB / 16; ++ks)
+                        tc_mma(tmem + ab * TC_N, sw128_desc(a0 + ks * 32), sw128_desc(b0 + ks * 32),
+                               (kb | ks) != 0 ? 1u : 0u);
                     tc_commit(&empty_s[s]);
                 }
                 if (!ok) { abort_sh = 1; break; }
-                tc_commit(&acc_full);
+                tc_commit(&acc_full[ab]);
             }
         }
     } else {
         // ---- epilogue: TMEM -> head sums in global memory (times 2^-20, rounded to FP16)
-        const int q = warp & 3, t = warp >> 2;
-        uint32_t v = 0;
-        for (int u = blockIdx.x; u < n_units && !abort_sh; u += gridDim.x, ++v) {
-            const int pair = u / a.n_cblk, cb = u - pair * a.n_cblk;
-            const bool ok = mbar_wait(&acc_full, v & 1);
+        // warp w drains TMEM lane quarter w % 4 of accumulator w / 4: the CTA's units
+        // v = w / 4, w / 4 + 2, ...
+        const int q = warp & 3, ab = warp >> 2;
+        uint32_t v = ab;
+        for (int u = blockIdx.x + ab * gridDim.x; u < n_units && !abort_sh; u += 2 * gridDim.x, v += 2) {
+            const int tile = u / a.n_cblk, cb = u - tile * a.n_cblk;
+            const bool ok = mbar_wait(&acc_full[ab], (v >> 1) & 1);
             if (__any_sync(FULL, !ok)) { abort_sh = 1; break; }
             tc_fence_after();
-            const int p = pair * HG_DOCS + t * TC_M + 32 * q + lane;
+            const int p = tile * HG_DOCS + 32 * q + lane;
             __half *dst = a.out + (int64_t)p * a.ld + (int64_t)cb * TC_N;
-            const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(t * TC_N);
+            const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * TC_N);
             constexpr float back = 1.0f / (TC_SCALE * TC_SCALE);   // 2^-20, exact
             // 64 columns per TMEM round trip: four loads in flight, one wait
             for (int c0 = 0; c0 < TC_N; c0 += 64) {
@@ -265,7 +269,8 @@ __global__ void __launch_bounds__(HG_THREADS, 1)
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&acc_empty)) : "memory");
+            if (lane == 0)
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&acc_empty[ab])) : "memory");
         }
     }
 
