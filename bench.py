@@ -423,7 +423,8 @@ def run_ours(args, w, world, rank, local, dist):
         checks["speedup_vs_fp32_full"] = fp32_full_speedup(skm, w, docs, ids, d_docs, args, local, stream, value)
         if w.name == workloads_large_name() and args.serve_check_seconds > 0:
             from paper_2108_00895_gb300 import workloads
-            checks["serving"] = serving_session(workloads.SERVING, local, args.serve_check_seconds, args.tau)
+            checks["serving"] = serving_session(workloads.SERVING, local, args.serve_check_seconds, args.tau,
+                                                job_slots=args.serve_job_slots)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -599,7 +600,7 @@ def run_batched(args, world, rank, local, dist):
 
 
 # ------------------------------------------------------------------ serving form
-def serving_session(W, local: int, window: float, tau: float, rates=None) -> dict:
+def serving_session(W, local: int, window: float, tau: float, rates=None, job_slots: int = 2) -> dict:
     """Serving form: open-loop Poisson arrivals against skm_server for a fixed window on a
     resident BF16 centroid set under the workload's device budget. Returns the latency,
     throughput and admission figures at the workload's offered rate; with `rates`, also one
@@ -621,11 +622,11 @@ def serving_session(W, local: int, window: float, tau: float, rates=None) -> dic
     resident.set_centroids(C)
     del C
     try:
-        out = _serving_window(W, local, window, tau, resident, pool, W.rate, True)
+        out = _serving_window(W, local, window, tau, resident, pool, W.rate, True, job_slots)
         if rates:
             sweep = []
             for r in rates:
-                o = _serving_window(W, local, window, tau, resident, pool, float(r), False)
+                o = _serving_window(W, local, window, tau, resident, pool, float(r), False, job_slots)
                 o.pop("queue_depth")
                 o.pop("clocks")
                 sweep.append(dict(rate=float(r), **o))
@@ -638,13 +639,13 @@ def serving_session(W, local: int, window: float, tau: float, rates=None) -> dic
     return out
 
 
-def _serving_window(W, local, window, tau, resident, pool, rate, sample_clocks) -> dict:
+def _serving_window(W, local, window, tau, resident, pool, rate, sample_clocks, job_slots) -> dict:
     """One open-loop window at `rate` requests/s on a fresh server over `resident`."""
     import math
 
     from paper_2108_00895_gb300 import skm, synth
     budget = int(W.budget_gb * (1 << 30))
-    srv = skm.Server(resident, budget, n_job_slots=2, max_batch_docs=65536, max_batch_nnz=65536 * 300,
+    srv = skm.Server(resident, budget, n_job_slots=job_slots, max_batch_docs=65536, max_batch_nnz=65536 * 300,
                      job_precision="bf16", job_prune="ncc", tau=tau, device=local)
     rng = np.random.default_rng(W.seed)
     rp, col, val = pool.row_ptr, pool.col_idx, pool.values
@@ -742,12 +743,13 @@ def run_serving(args, world, rank, local, dist):
     torch.cuda.set_device(torch.device("cuda", local))
     skm.load()
     rates = [float(r) for r in args.serve_rates.split(",")] if args.serve_rates else None
-    sv = serving_session(W, local, args.serve_seconds, args.tau, rates)
+    sv = serving_session(W, local, args.serve_seconds, args.tau, rates, args.serve_job_slots)
     clk = sv.pop("clocks")
     line = {"metric": "serving docs assigned/s; p50/p99 assignment latency (ms)", "value": sv["assign_docs_per_s"],
             "unit": "docs/s", "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": 1e3 * sv["drain_seconds"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": dict(W.describe(), window_s=args.serve_seconds, job_slots=2, max_batch_docs=65536),
+            "config": dict(W.describe(), window_s=args.serve_seconds, job_slots=args.serve_job_slots,
+                           max_batch_docs=65536),
             "serving": sv, "clocks": clk,
             "e2e": {"value": sv["assign_docs_per_s"], "unit": "docs/s", "h2d_bytes_per_step": None,
                     "d2h_bytes_per_step": None}}
@@ -766,6 +768,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving window (open loop)")
     ap.add_argument("--serve-rates", default="50,100,250,500,1000,2000,4000",
                     help="serving workload: also one window per offered rate (requests/s, comma list; '' = none)")
+    ap.add_argument("--serve-job-slots", type=int, default=2, help="serving: clustering jobs run at once")
     ap.add_argument("--tau", type=float, default=1e-4)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
