@@ -702,7 +702,6 @@ TiQueryArgs ti_args(skm_ctx *ctx, const DevCsr &dc) {
     q.gptr = P<int64_t>(ctx->ti_gptr);
     q.pbe = P<uint32_t>(ctx->ti_pbe);
     q.L = ctx->cfg.index_levels;
-    q.elt = ctx->cfg.precision == SKM_BF16 ? 2 : 4;
     q.max_cands = ctx->cfg.index_max_cands;
     for (int l = 0; l < q.L; ++l) q.lam[l] = ctx->cfg.index_lambda[l];
     q.fixed_level = -1;

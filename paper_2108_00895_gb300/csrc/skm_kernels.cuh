@@ -252,7 +252,6 @@ struct TiQueryArgs {
     const int64_t *gptr;        // [d + 1] row offsets of G's nonzeros
     const uint32_t *pbe;        // [L][d][TI_MB] bucket ends of each term's list
     int L;
-    int elt;                    // bytes per entry of the dense scored copy (2 BF16, 4 FP32)
     int max_cands;              // candidate cap (at most TI_CAND); 0: TI_CAND
     double lam[TI_MAXL];        // ascending
     int fixed_level;            // >= 0: candidate dump at this level (no baseline, no scoring)
