@@ -600,6 +600,15 @@ def run_batched(args, world, rank, local, dist):
 
 
 # ------------------------------------------------------------------ serving form
+def sustained_rate(sweep, max_waiting: float = 0.1):
+    """The largest offered rate of a sweep at which every assignment was served and at most
+    max_waiting of the clustering jobs were still waiting at the end of the window (None if
+    no rate qualifies)."""
+    ok = [o["rate"] for o in sweep
+          if o["assign_done"] == o["assign_requests"] and (o["fit_deferred_fraction"] or 0.0) <= max_waiting]
+    return max(ok) if ok else None
+
+
 def serving_session(W, local: int, window: float, tau: float, rates=None, job_slots: int = 2) -> dict:
     """Serving form: open-loop Poisson arrivals against skm_server for a fixed window on a
     resident BF16 centroid set under the workload's device budget. Returns the latency,
@@ -631,9 +640,7 @@ def serving_session(W, local: int, window: float, tau: float, rates=None, job_sl
                 o.pop("clocks")
                 sweep.append(dict(rate=float(r), **o))
             out["rate_sweep"] = sweep
-            ok = [o["rate"] for o in sweep
-                  if o["assign_done"] == o["assign_requests"] and (o["fit_deferred_fraction"] or 0.0) <= 0.1]
-            out["sustained_rate"] = max(ok) if ok else None
+            out["sustained_rate"] = sustained_rate(sweep)
     finally:
         resident.close()
     return out
