@@ -262,9 +262,6 @@ __device__ __forceinline__ void slice_accumulate_sparse(int64_t beg, int64_t end
     }
 }
 
-// The slice's best TOPT (score, centroid id) of a warp's accumulators, written by lanes
-// 0..TOPT-1 to part_s/part_j[o + lane]. Columns at or beyond ncols are ignored; col_ids maps
-// a column to its centroid id (NULL: identity).
 // The warp's best TOPT over the lanes' best-first lists, in TOPT rounds: the largest score,
 // then the smallest id among the lanes that hold it; the winning lane drops its head. Scores
 // are non-negative, so their bit patterns order like their values and one warp reduction
@@ -302,8 +299,10 @@ __device__ __forceinline__ void topt_warp_select(float (&ls)[TOPT], int (&lj)[TO
     }
 }
 
-// The slice's best TOPT (score, centroid id) to part_s / part_j [o, o + TOPT). Only columns
-// that can be among them are sorted into the lanes' lists: with T the TOPT-th largest of the
+// The slice's best TOPT (score, centroid id) of a warp's accumulators, written by lanes
+// 0..TOPT-1 to part_s/part_j[o + lane]. Columns at or beyond ncols are ignored; col_ids maps
+// a column to its centroid id (NULL: identity). Only columns that can be among them are
+// sorted into the lanes' lists: with T the TOPT-th largest of the
 // 32 lanes' maxima, TOPT columns (those maxima) score at least T, so every column of the
 // result does too. Scores are non-negative and compare as their bit patterns. When fewer than
 // TOPT lanes hold a positive score (T = 0), every column goes into the lists.
