@@ -300,12 +300,12 @@ __device__ __forceinline__ void topt_warp_select(float (&ls)[TOPT], int (&lj)[TO
 }
 
 // The slice's best TOPT (score, centroid id) of a warp's accumulators, written by lanes
-// 0..TOPT-1 to part_s/part_j[o + lane]. Columns at or beyond ncols are ignored; col_ids maps
-// a column to its centroid id (NULL: identity). Only columns that can be among them are
-// sorted into the lanes' lists: with T the TOPT-th largest of the
-// 32 lanes' maxima, TOPT columns (those maxima) score at least T, so every column of the
-// result does too. Scores are non-negative and compare as their bit patterns. When fewer than
-// TOPT lanes hold a positive score (T = 0), every column goes into the lists.
+// 0..TOPT-1 to part_s/part_j[o + lane]. Columns at or beyond ncols are ignored; col_ids
+// maps a column to its centroid id (NULL: identity). Only columns that can be among them
+// are sorted into the lanes' lists: with T the TOPT-th largest of the 32 lanes' maxima,
+// TOPT columns (those maxima) score at least T, so every column of the result does too.
+// Scores are non-negative and compare as their bit patterns. When fewer than TOPT lanes
+// hold a positive score (T = 0), every column goes into the lists.
 template <typename CT, int NV>
 __device__ __forceinline__ void slice_topt_write(const float2 (&acc)[NV * 16 / (int)sizeof(CT) / 2], int64_t j0,
                                                  int lane, int32_t ncols, const int32_t *col_ids, float *part_s,
